@@ -1,0 +1,214 @@
+/*
+ * abfs -- algebraic breadth-first search by submatrix multiplication on GB300.
+ *
+ * The method (Burkhardt, "Optimal algebraic Breadth-First Search for sparse
+ * graphs"): BFS is the recurrence x_{k+1} = A[V_{k+1}, V_k] x_k (Theorem 1),
+ * where V_k holds the vertices not yet reached before step k (Definition 1).
+ * Each frontier column is multiplied once (Claim 1), and the rows of visited
+ * vertices are masked out before the multiply, so the matrix shrinks as the
+ * search advances (Section 6, Section 7).  Algorithm 1 (Section 8) gives the
+ * general loop; Algorithm 3 (Section 10) the parallel form.
+ *
+ * Graph layout.  A graph is given in compressed sparse column form of A^T:
+ * column j (rowidx[colptr[j] .. colptr[j+1]-1]) lists the out-neighbours of
+ * vertex j.  For undirected graphs A = A^T and column j lists j's
+ * neighbours; Section 7 uses A^T for directed graphs.  Vertices are 0..n-1.
+ * colptr is uint32[n+1] with colptr[0] = 0, non-decreasing, colptr[n] = nnz;
+ * rowidx is uint32[nnz] with every entry < n.  Duplicates and self-loops are
+ * allowed and do not change any result.
+ *
+ * Results.  level[v] is the hop distance from the source (0 at the source),
+ * -1 if v is unreachable.  parent[v] is the least-index predecessor of v on
+ * the previous level (min{ j : v in column j, level[j] = level[v] - 1 }),
+ * parent[source] = source, -1 if unreachable.  The paper allows any write
+ * resolution among concurrent parents (Theorem 4, Section 10); this library
+ * always takes the minimum index, so results are a pure function of the graph
+ * and are identical across runs, modes and batch mixes.
+ *
+ * Errors.  Every call returns an int status (abfs_status).  No C++ exception
+ * crosses this boundary.  abfs_strerror() turns a status into text.
+ *
+ * Streams.  abfs_stream_t is a cudaStream_t passed as an opaque pointer (NULL
+ * is the legacy default stream).  Device work is enqueued on that stream and
+ * runs asynchronously unless a call says it synchronises.
+ *
+ * Device.  Objects belong to the CUDA device that was current when they were
+ * created; calls on them must be made with that device current.
+ */
+#ifndef ABFS_H
+#define ABFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* abfs_stream_t;
+typedef struct abfs_graph_s* abfs_graph_t;
+typedef struct abfs_batch_s* abfs_batch_t;
+typedef struct abfs_server_s* abfs_server_t;
+
+typedef enum {
+    ABFS_OK = 0,
+    ABFS_ERR_INVALID_ARG = 1,   /* null pointer, source >= n, malformed CSC, bad parameter */
+    ABFS_ERR_NOT_SYMMETRIC = 2, /* directed = 0 with ABFS_VALIDATE, but A != A^T */
+    ABFS_ERR_OOM = 3,           /* a device or host allocation failed */
+    ABFS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    ABFS_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out; the kernel returned */
+    ABFS_ERR_BUSY = 6,          /* serving: the request was not admitted (no slot / memory) */
+    ABFS_ERR_DEVICE = 7,        /* a device-side consistency check failed (capacity, bounds) */
+    ABFS_ERR_UNSUPPORTED = 8,   /* size beyond this build's limits */
+    ABFS_ERR_NOT_FOUND = 9      /* serving: unknown ticket */
+} abfs_status;
+
+/* abfs_graph_create flags */
+#define ABFS_VALIDATE 1u        /* check colptr/rowidx (and symmetry when directed = 0) */
+#define ABFS_INPUT_ON_DEVICE 2u /* colptr/rowidx are device pointers (else host pointers) */
+
+/* Execution modes (abfs_params.mode). */
+#define ABFS_MODE_SUBMATRIX 0u  /* the paper's method: mask rows, then multiply */
+#define ABFS_MODE_PLAIN 1u      /* comparator: masked SpMSpV, multiply every entry, mask after */
+
+/* Tunable launch parameters.  abfs_default_params() fills sound values;
+ * abfs_tune() measures and picks them for a graph. */
+typedef struct {
+    uint32_t mode;            /* ABFS_MODE_SUBMATRIX or ABFS_MODE_PLAIN */
+    uint32_t tile;            /* frontier vertices per work unit, 32..2048, multiple of 32 */
+    uint32_t heavy_degree;    /* columns with >= this many entries are split into chunks */
+    uint32_t chunk;           /* entries per heavy-column chunk, multiple of 128 */
+    uint32_t narrow_max;      /* frontiers of <= this many vertices run on one CTA; <= tile */
+    uint32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x SM count (capped by occupancy) */
+    float shrink_theta;       /* physical shrink once the reached fraction of n crosses theta;
+                                 <= 0 or >= 1 disables it */
+    uint32_t shrink_max;      /* at most this many shrinks per search */
+    uint32_t timeout_ms;      /* bound on any device-side wait without progress */
+} abfs_params;
+
+/* Per-search counters, filled when a stats pointer is passed. */
+typedef struct {
+    uint32_t levels;              /* non-empty frontiers (eccentricity of the source + 1) */
+    uint32_t reached;             /* n_c: vertices reached, source included */
+    uint64_t nnz_reached;         /* nnz_c: sum of the reached columns' lengths in the input */
+    uint64_t entries_read;        /* stored entries read by the expansion (shrunk matrix after a shrink) */
+    uint64_t entries_unmasked;    /* entries whose row passed the visited mask (multiplied) */
+    uint64_t claims;              /* atomic claim attempts (parent updates issued) */
+    uint32_t shrinks;             /* physical shrink events */
+    uint32_t wide_levels;         /* levels run across the whole grid */
+    uint64_t shrink_entries_read; /* entries read by shrink kernels */
+    uint64_t shrink_entries_kept; /* entries written by shrink kernels */
+    uint32_t status;              /* abfs_status of the device side */
+    uint32_t reserved;
+} abfs_stats;
+
+/* Returns a static string for a status code. */
+const char* abfs_strerror(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int abfs_version(void);
+
+/* Fills *p with defaults (submatrix mode, no shrink). */
+int abfs_default_params(abfs_params* p);
+
+/*
+ * Creates a device-resident graph from CSC arrays (Section 9's compressed
+ * format, applied to A^T).  The arrays are copied: the caller keeps ownership
+ * of colptr/rowidx, and the library owns the result until
+ * abfs_graph_destroy().  With ABFS_INPUT_ON_DEVICE the pointers are device
+ * pointers; otherwise host pointers.  With ABFS_VALIDATE the CSC invariants
+ * (and, for directed = 0, symmetry of the pattern) are checked on the host
+ * (for device input, after a copy back).  `directed` does not change the
+ * traversal; it selects validation and the edge convention of reports.
+ * Synchronises `stream` before returning.
+ * Limits: n < 2^31, nnz < 2^32.
+ */
+int abfs_graph_create(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, uint64_t nnz,
+                      int directed, uint32_t flags, abfs_stream_t stream, abfs_graph_t* out);
+
+int abfs_graph_destroy(abfs_graph_t g);
+
+/* n, nnz and the directed flag of a graph (any pointer may be NULL). */
+int abfs_graph_info(abfs_graph_t g, uint32_t* n, uint64_t* nnz, int* directed);
+
+/* Device bytes one search on this graph needs beyond the graph itself
+ * (bitmaps, frontier queues, control), for the given parameters
+ * (NULL = defaults).  Serving admission uses this figure. */
+int abfs_graph_footprint(abfs_graph_t g, const abfs_params* params, size_t* bytes_per_query);
+
+/*
+ * One BFS from `source` (Algorithm 1 / Theorem 1): writes level[0..n-1] and
+ * parent[0..n-1], caller-owned DEVICE buffers of n int32 each.  Asynchronous
+ * on `stream` unless `stats` is non-NULL, in which case it synchronises and
+ * fills *stats.  params = NULL uses the graph's tuned parameters if
+ * abfs_tune() ran, else defaults.  The graph keeps one search workspace;
+ * calls on the same graph are ordered on the GPU (a later call on another
+ * stream waits for the earlier one).
+ */
+int abfs_run(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,
+             abfs_stream_t stream, const abfs_params* params, abfs_stats* stats);
+
+/*
+ * Same search, end to end through host memory: copies the source in, runs,
+ * and copies level/parent back into HOST buffers of n int32 each (pinned
+ * memory gives full copy bandwidth).  Synchronises `stream`.
+ */
+int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_host, int32_t* parent_host,
+                  abfs_stream_t stream, const abfs_params* params, abfs_stats* stats);
+
+/*
+ * Batched search: `count` independent searches (graph g[i], source
+ * sources[i]) in ONE persistent launch with per-instance frontier queues;
+ * each CTA takes work units from any instance that has them.  level[i] and
+ * parent[i] are caller-owned DEVICE buffers of g[i]'s n int32 each.
+ * status_per_query (host, count entries, may be NULL) receives each search's
+ * abfs_status.  Synchronises `stream`.  Results equal abfs_run's, bit for
+ * bit.
+ */
+int abfs_run_batch(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
+                   int32_t* const* level, int32_t* const* parent, abfs_stream_t stream,
+                   const abfs_params* params, int32_t* status_per_query);
+
+/*
+ * Reusable batch plan: allocates the per-instance workspaces once and
+ * captures the initialisation and the persistent launch in a CUDA graph
+ * (captured on `stream` at creation).  abfs_batch_launch() replays it; the
+ * output pointers given here are written on every replay.  The plan keeps
+ * references to the graphs, which must outlive it.
+ */
+int abfs_batch_create(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
+                      int32_t* const* level, int32_t* const* parent, const abfs_params* params,
+                      abfs_stream_t stream, abfs_batch_t* out);
+int abfs_batch_launch(abfs_batch_t b, abfs_stream_t stream);
+/* Copies per-instance statuses (host array of count) after a launch; synchronises. */
+int abfs_batch_status(abfs_batch_t b, abfs_stream_t stream, int32_t* status_per_query);
+int abfs_batch_destroy(abfs_batch_t b);
+
+/*
+ * Autotuner: times candidate parameter sets on `count` searches from
+ * `sources` and stores the fastest in the graph (used when params = NULL).
+ * `mode` selects which method is tuned.  *best (may be NULL) receives the
+ * choice and *best_ms its mean device time per search.  With `cache_path`
+ * non-NULL the result is read from / appended to that JSON-lines file, keyed
+ * by GPU name, SM count, mode and the graph's size class.  Synchronises.
+ */
+int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count, uint32_t mode,
+              const char* cache_path, abfs_stream_t stream, abfs_params* best, float* best_ms);
+
+/*
+ * Device-memory hook: alloc(bytes, ctx) returns device memory or NULL;
+ * free_fn(ptr, ctx) releases it.  Both NULL restores cudaMalloc/cudaFree.
+ * Applies to allocations made after the call (graphs, workspaces, plans);
+ * memory must be freed by the hook that allocated it.
+ */
+int abfs_set_allocator(void* (*alloc)(size_t bytes, void* ctx), void (*free_fn)(void* ptr, void* ctx),
+                       void* ctx);
+
+/* Text of the last CUDA runtime error seen by this thread ("" if none). */
+const char* abfs_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABFS_H */

@@ -1,0 +1,348 @@
+"""Thin ctypes binding over libabfs.so (the C-ABI in include/abfs.h).
+
+Argument marshalling only: every step of a search runs in the library's CUDA
+kernels.  PyTorch supplies device memory (output tensors) and streams.  The
+binding loads the in-tree libabfs.so and raises if it is missing; there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libabfs.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "abfs.h")
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_NOT_SYMMETRIC = 2
+ERR_OOM = 3
+ERR_CUDA = 4
+ERR_TIMEOUT = 5
+ERR_BUSY = 6
+ERR_DEVICE = 7
+ERR_UNSUPPORTED = 8
+ERR_NOT_FOUND = 9
+
+VALIDATE = 1
+INPUT_ON_DEVICE = 2
+MODE_SUBMATRIX = 0
+MODE_PLAIN = 1
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_uint32),
+        ("tile", ctypes.c_uint32),
+        ("heavy_degree", ctypes.c_uint32),
+        ("chunk", ctypes.c_uint32),
+        ("narrow_max", ctypes.c_uint32),
+        ("ctas_per_sm", ctypes.c_uint32),
+        ("shrink_theta", ctypes.c_float),
+        ("shrink_max", ctypes.c_uint32),
+        ("timeout_ms", ctypes.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_uint32),
+        ("reached", ctypes.c_uint32),
+        ("nnz_reached", ctypes.c_uint64),
+        ("entries_read", ctypes.c_uint64),
+        ("entries_unmasked", ctypes.c_uint64),
+        ("claims", ctypes.c_uint64),
+        ("shrinks", ctypes.c_uint32),
+        ("wide_levels", ctypes.c_uint32),
+        ("shrink_entries_read", ctypes.c_uint64),
+        ("shrink_entries_kept", ctypes.c_uint64),
+        ("status", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+class AbfsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.abfs_strerror(status).decode() if _lib else str(status)
+        extra = ""
+        if status == ERR_CUDA and _lib:
+            extra = " (" + _lib.abfs_last_cuda_error().decode() + ")"
+        super().__init__(f"{where}: {msg}{extra} [status {status}]")
+
+
+_lib = None
+
+
+def declared_symbols() -> list[str]:
+    """Every function name include/abfs.h declares."""
+    text = open(HEADER_PATH).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(abfs_[a-z_0-9]+)\s*\(", text)))
+
+
+def load():
+    """Loads libabfs.so (built by __graft_entry__.build()); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p
+    c_int = ctypes.c_int
+    sig = {
+        "abfs_strerror": ([c_int], ctypes.c_char_p),
+        "abfs_last_cuda_error": ([], ctypes.c_char_p),
+        "abfs_version": ([], c_int),
+        "abfs_default_params": ([P(Params)], c_int),
+        "abfs_graph_create": ([vp, vp, u32, u64, c_int, u32, vp, P(vp)], c_int),
+        "abfs_graph_destroy": ([vp], c_int),
+        "abfs_graph_info": ([vp, P(u32), P(u64), P(c_int)], c_int),
+        "abfs_graph_footprint": ([vp, P(Params), P(ctypes.c_size_t)], c_int),
+        "abfs_run": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
+        "abfs_run_host": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
+        "abfs_run_batch": ([P(vp), P(u32), u32, P(vp), P(vp), vp, P(Params), P(i32)], c_int),
+        "abfs_batch_create": ([P(vp), P(u32), u32, P(vp), P(vp), P(Params), vp, P(vp)], c_int),
+        "abfs_batch_launch": ([vp, vp], c_int),
+        "abfs_batch_status": ([vp, vp, P(i32)], c_int),
+        "abfs_batch_destroy": ([vp], c_int),
+        "abfs_tune": ([vp, P(u32), u32, u32, ctypes.c_char_p, vp, P(Params),
+                       P(ctypes.c_float)], c_int),
+        "abfs_set_allocator": ([vp, vp, vp], c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != OK:
+        raise AbfsError(rc, where)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    _check(load().abfs_default_params(ctypes.byref(p)), "abfs_default_params")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def strerror(status: int) -> str:
+    return load().abfs_strerror(status).decode()
+
+
+# ---------------------------------------------------------------------------
+# graphs
+# ---------------------------------------------------------------------------
+
+class Graph:
+    """A device-resident graph (abfs_graph_t).  Column j of the CSC lists the
+    out-neighbours of j."""
+
+    def __init__(self, handle: int, n: int, nnz: int, directed: bool):
+        self.handle = ctypes.c_void_p(handle)
+        self.n, self.nnz, self.directed = n, nnz, directed
+
+    def destroy(self) -> None:
+        if self.handle and self.handle.value:
+            _check(load().abfs_graph_destroy(self.handle), "abfs_graph_destroy")
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            if _lib is not None and self.handle and self.handle.value:
+                _lib.abfs_graph_destroy(self.handle)
+        except Exception:
+            pass
+
+    def footprint(self, params: Params | None = None) -> int:
+        out = ctypes.c_size_t()
+        _check(load().abfs_graph_footprint(self.handle, ctypes.byref(params) if params else None,
+                                           ctypes.byref(out)), "abfs_graph_footprint")
+        return int(out.value)
+
+
+def graph_create(colptr, rowidx, directed: bool = False, validate: bool = False,
+                 stream=None) -> Graph:
+    """From host numpy arrays (uint32) or CUDA tensors (int32/uint32 bits)."""
+    lib = load()
+    flags = VALIDATE if validate else 0
+    if isinstance(colptr, np.ndarray):
+        colptr = np.ascontiguousarray(colptr, dtype=np.uint32)
+        rowidx = np.ascontiguousarray(rowidx, dtype=np.uint32)
+        n = colptr.shape[0] - 1
+        nnz = rowidx.shape[0]
+        cp, rp = colptr.ctypes.data, (rowidx.ctypes.data if nnz else None)
+        keep = (colptr, rowidx)
+    else:  # torch tensors on the device
+        flags |= INPUT_ON_DEVICE
+        n = colptr.numel() - 1
+        nnz = rowidx.numel()
+        cp, rp = colptr.data_ptr(), (rowidx.data_ptr() if nnz else None)
+        keep = (colptr, rowidx)
+    h = ctypes.c_void_p()
+    rc = lib.abfs_graph_create(cp, rp, n, nnz, 1 if directed else 0, flags, _stream_ptr(stream),
+                               ctypes.byref(h))
+    del keep
+    _check(rc, "abfs_graph_create")
+    return Graph(h.value, n, nnz, directed)
+
+
+def graph_destroy(g: Graph) -> None:
+    g.destroy()
+
+
+# ---------------------------------------------------------------------------
+# searches
+# ---------------------------------------------------------------------------
+
+def _outputs(n: int, level, parent, device):
+    import torch
+    if level is None:
+        level = torch.empty(n, dtype=torch.int32, device=device)
+    if parent is None:
+        parent = torch.empty(n, dtype=torch.int32, device=device)
+    assert level.dtype == torch.int32 and parent.dtype == torch.int32
+    assert level.is_cuda and parent.is_cuda and level.numel() >= n and parent.numel() >= n
+    return level, parent
+
+
+def run(g: Graph, source: int, level=None, parent=None, stream=None, params: Params | None = None,
+        stats: bool = False):
+    """abfs_run: returns (level, parent) CUDA int32 tensors (and a stats dict)."""
+    import torch
+    level, parent = _outputs(g.n, level, parent, torch.device("cuda", torch.cuda.current_device()))
+    st = Stats() if stats else None
+    rc = load().abfs_run(g.handle, int(source), level.data_ptr(), parent.data_ptr(),
+                         _stream_ptr(stream), ctypes.byref(params) if params else None,
+                         ctypes.byref(st) if st else None)
+    _check(rc, "abfs_run")
+    return (level, parent, st.as_dict()) if stats else (level, parent)
+
+
+def run_host(g: Graph, source: int, level_host: np.ndarray | None = None,
+             parent_host: np.ndarray | None = None, stream=None, params: Params | None = None,
+             stats: bool = False):
+    """abfs_run_host: results in host arrays (pinned tensors give full copy speed)."""
+    if level_host is None:
+        level_host = np.empty(g.n, dtype=np.int32)
+    if parent_host is None:
+        parent_host = np.empty(g.n, dtype=np.int32)
+    lp = level_host.ctypes.data if isinstance(level_host, np.ndarray) else level_host.data_ptr()
+    pp = parent_host.ctypes.data if isinstance(parent_host, np.ndarray) else parent_host.data_ptr()
+    st = Stats() if stats else None
+    rc = load().abfs_run_host(g.handle, int(source), lp, pp, _stream_ptr(stream),
+                              ctypes.byref(params) if params else None,
+                              ctypes.byref(st) if st else None)
+    _check(rc, "abfs_run_host")
+    return (level_host, parent_host, st.as_dict()) if stats else (level_host, parent_host)
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+def run_batch(graphs: list[Graph], sources, levels=None, parents=None, stream=None,
+              params: Params | None = None):
+    """abfs_run_batch: one persistent launch for all searches.  Returns
+    (levels, parents, statuses)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    count = len(graphs)
+    levels = levels or [torch.empty(g.n, dtype=torch.int32, device=dev) for g in graphs]
+    parents = parents or [torch.empty(g.n, dtype=torch.int32, device=dev) for g in graphs]
+    src = (ctypes.c_uint32 * count)(*[int(s) for s in sources])
+    st = (ctypes.c_int32 * count)()
+    rc = load().abfs_run_batch(_ptr_array([g.handle.value for g in graphs]), src, count,
+                               _ptr_array([t.data_ptr() for t in levels]),
+                               _ptr_array([t.data_ptr() for t in parents]), _stream_ptr(stream),
+                               ctypes.byref(params) if params else None, st)
+    statuses = list(st)
+    if rc not in (OK, ERR_TIMEOUT, ERR_DEVICE):
+        _check(rc, "abfs_run_batch")
+    return levels, parents, statuses
+
+
+class BatchPlan:
+    """abfs_batch_create / launch / status / destroy: workspaces allocated once,
+    initialisation + persistent launch captured in a CUDA graph."""
+
+    def __init__(self, graphs: list[Graph], sources, levels=None, parents=None,
+                 params: Params | None = None, stream=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.graphs = list(graphs)
+        self.count = len(graphs)
+        self.levels = levels or [torch.empty(g.n, dtype=torch.int32, device=dev) for g in graphs]
+        self.parents = parents or [torch.empty(g.n, dtype=torch.int32, device=dev) for g in graphs]
+        src = (ctypes.c_uint32 * self.count)(*[int(s) for s in sources])
+        h = ctypes.c_void_p()
+        rc = load().abfs_batch_create(_ptr_array([g.handle.value for g in graphs]), src, self.count,
+                                      _ptr_array([t.data_ptr() for t in self.levels]),
+                                      _ptr_array([t.data_ptr() for t in self.parents]),
+                                      ctypes.byref(params) if params else None,
+                                      _stream_ptr(stream), ctypes.byref(h))
+        _check(rc, "abfs_batch_create")
+        self.handle = h
+
+    def launch(self, stream=None) -> None:
+        _check(load().abfs_batch_launch(self.handle, _stream_ptr(stream)), "abfs_batch_launch")
+
+    def status(self, stream=None) -> list[int]:
+        st = (ctypes.c_int32 * self.count)()
+        load().abfs_batch_status(self.handle, _stream_ptr(stream), st)
+        return list(st)
+
+    def destroy(self) -> None:
+        if self.handle and self.handle.value:
+            _check(load().abfs_batch_destroy(self.handle), "abfs_batch_destroy")
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            if _lib is not None and self.handle and self.handle.value:
+                _lib.abfs_batch_destroy(self.handle)
+        except Exception:
+            pass
+
+
+def tune(g: Graph, sources, mode: int = MODE_SUBMATRIX, cache_path: str | None = None,
+         stream=None):
+    """abfs_tune: returns (best Params, mean ms per search)."""
+    count = len(sources)
+    src = (ctypes.c_uint32 * count)(*[int(s) for s in sources])
+    best = Params()
+    ms = ctypes.c_float()
+    rc = load().abfs_tune(g.handle, src, count, mode,
+                          cache_path.encode() if cache_path else None, _stream_ptr(stream),
+                          ctypes.byref(best), ctypes.byref(ms))
+    _check(rc, "abfs_tune")
+    return best, float(ms.value)

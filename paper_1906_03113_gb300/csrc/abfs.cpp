@@ -1,0 +1,868 @@
+// Host runtime behind the C-ABI declared in include/abfs.h: graph storage and
+// validation, search workspaces, single and batched searches, the autotuner.
+// Every step of a search runs in the device engine (engine.cu); this file only
+// allocates, initialises descriptors and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/abfs.h"
+#include "internal.h"
+
+using namespace abfs;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+
+extern "C" const char* abfs_strerror(int status) {
+    switch (status) {
+        case ABFS_OK: return "ok";
+        case ABFS_ERR_INVALID_ARG: return "invalid argument";
+        case ABFS_ERR_NOT_SYMMETRIC: return "graph marked undirected is not symmetric";
+        case ABFS_ERR_OOM: return "out of memory";
+        case ABFS_ERR_CUDA: return "CUDA runtime error";
+        case ABFS_ERR_TIMEOUT: return "bounded device wait expired";
+        case ABFS_ERR_BUSY: return "not admitted: no free slot or memory";
+        case ABFS_ERR_DEVICE: return "device-side consistency check failed";
+        case ABFS_ERR_UNSUPPORTED: return "size beyond this build's limits";
+        case ABFS_ERR_NOT_FOUND: return "unknown ticket";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int abfs_version(void) { return 10000; }
+
+namespace {
+
+thread_local std::string g_last_cuda_error;
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return ABFS_OK;
+    g_last_cuda_error = cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return ABFS_ERR_OOM;
+    return ABFS_ERR_CUDA;
+}
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// allocator hook
+// ---------------------------------------------------------------------------
+
+struct Allocator {
+    void* (*alloc)(size_t, void*) = nullptr;
+    void (*free)(void*, void*) = nullptr;
+    void* ctx = nullptr;
+};
+Allocator g_alloc;
+std::mutex g_alloc_mu;
+
+int dev_alloc(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    Allocator a;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+    }
+    if (a.alloc) {
+        *p = a.alloc(bytes, a.ctx);
+        return *p ? ABFS_OK : ABFS_ERR_OOM;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? ABFS_ERR_OOM : cuda_fail(e);
+    }
+    return ABFS_OK;
+}
+
+void dev_free(void* p) {
+    if (!p) return;
+    Allocator a;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+    }
+    if (a.free) a.free(p, a.ctx);
+    else cudaFree(p);
+}
+
+// ---------------------------------------------------------------------------
+// parameters
+// ---------------------------------------------------------------------------
+
+abfs_params default_params() {
+    abfs_params p;
+    p.mode = ABFS_MODE_SUBMATRIX;
+    p.tile = 1024;
+    p.heavy_degree = 4096;
+    p.chunk = 4096;
+    p.narrow_max = 1024;
+    p.ctas_per_sm = 2;
+    p.shrink_theta = 0.f;
+    p.shrink_max = 0;
+    p.timeout_ms = 10000;
+    return p;
+}
+
+bool shrink_enabled(const abfs_params& p) {
+    return p.mode == ABFS_MODE_SUBMATRIX && p.shrink_theta > 0.f && p.shrink_theta < 1.f &&
+           p.shrink_max > 0;
+}
+
+int check_params(const abfs_params& p) {
+    if (p.mode > ABFS_MODE_PLAIN) return ABFS_ERR_INVALID_ARG;
+    if (p.tile < 32 || p.tile > (uint32_t)kTileMax || p.tile % 32) return ABFS_ERR_INVALID_ARG;
+    if (p.chunk < 128 || p.chunk % 128 || p.chunk > (1u << 24)) return ABFS_ERR_INVALID_ARG;
+    if (p.heavy_degree < p.chunk) return ABFS_ERR_INVALID_ARG;
+    if (p.narrow_max > p.tile) return ABFS_ERR_INVALID_ARG;
+    if (p.ctas_per_sm < 1 || p.ctas_per_sm > 8) return ABFS_ERR_INVALID_ARG;
+    if (!(p.shrink_theta >= 0.f) || p.shrink_theta > 1.f) return ABFS_ERR_INVALID_ARG;
+    if (p.timeout_ms < 1 || p.timeout_ms > 600000) return ABFS_ERR_INVALID_ARG;
+    return ABFS_OK;
+}
+
+EngineParams engine_params(const abfs_params& p) {
+    EngineParams e;
+    e.mode = p.mode;
+    e.tile = p.tile;
+    e.heavy = p.heavy_degree;
+    e.chunk = p.chunk;
+    e.narrow_max = p.narrow_max;
+    e.shrink_theta = shrink_enabled(p) ? p.shrink_theta : 0.f;
+    e.shrink_max = shrink_enabled(p) ? std::min<uint32_t>(p.shrink_max, 64) : 0;
+    e.shrink_tile = kTileMax;
+    e.timeout_ns = (unsigned long long)p.timeout_ms * 1000000ull;
+    return e;
+}
+
+bool same_layout(const abfs_params& a, const abfs_params& b) {
+    return a.mode == b.mode && a.chunk == b.chunk && a.heavy_degree == b.heavy_degree &&
+           shrink_enabled(a) == shrink_enabled(b) &&
+           (!shrink_enabled(a) || std::min(a.shrink_max, 2u) == std::min(b.shrink_max, 2u));
+}
+
+// ---------------------------------------------------------------------------
+// per-search workspace layout
+// ---------------------------------------------------------------------------
+
+struct Layout {
+    size_t bm[2], fq[2], hq[2], y, touched, sbeg[2], slen[2], srows[2], ctl, inst;
+    size_t total;
+    uint32_t nwords, hcap, ncopies;
+    unsigned long long scap;
+};
+
+Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p) {
+    Layout L;
+    std::memset(&L, 0, sizeof(L));
+    const size_t A = 256;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, A);
+        return at;
+    };
+    L.nwords = (n + 31) / 32;
+    L.hcap = (uint32_t)std::min<uint64_t>(2 * nnz / p.chunk + 64, 0xFFFFFFF0ull);
+    L.ctl = take(sizeof(InstCtl));
+    L.inst = take(sizeof(Inst));
+    for (int i = 0; i < 2; ++i) L.fq[i] = take((size_t)n * 4);
+    for (int i = 0; i < 2; ++i) L.hq[i] = take((size_t)L.hcap * 8);
+    if (p.mode == ABFS_MODE_SUBMATRIX)
+        for (int i = 0; i < 2; ++i) L.bm[i] = take((size_t)L.nwords * 4);
+    if (p.mode == ABFS_MODE_PLAIN) {
+        L.y = take((size_t)n * 8);
+        L.touched = take((size_t)n * 4);
+    }
+    if (shrink_enabled(p)) {
+        L.ncopies = std::min(p.shrink_max, 2u);
+        L.scap = nnz;
+        for (uint32_t i = 0; i < L.ncopies; ++i) {
+            L.sbeg[i] = take((size_t)n * 4);
+            L.slen[i] = take((size_t)n * 4);
+            L.srows[i] = take((size_t)std::max<uint64_t>(nnz, 1) * 4);
+        }
+    }
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// graph
+// ---------------------------------------------------------------------------
+
+struct Workspace {
+    char* base = nullptr;
+    Layout L{};
+    abfs_params p{};
+    Inst* d_inst = nullptr;   // device descriptor (instance 0)
+    uint32_t* d_done = nullptr;
+    unsigned long long* d_beat = nullptr;
+    InstCtl* h_ctl = nullptr; // pinned copy for stats
+    int32_t* d_level = nullptr;   // for host-output runs
+    int32_t* d_parent = nullptr;
+};
+
+struct abfs_graph_s {
+    uint32_t* d_colptr = nullptr;
+    uint32_t* d_rowidx = nullptr;
+    uint32_t n = 0;
+    uint64_t nnz = 0;
+    int directed = 0;
+    int device = 0;
+    int sms = 0;
+    bool tuned = false;
+    abfs_params tuned_params{};
+    std::mutex mu;
+    Workspace ws;
+    cudaEvent_t last_use = nullptr;
+    bool used = false;
+};
+
+namespace {
+
+int validate_host(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, uint64_t nnz,
+                  int directed) {
+    if (colptr[0] != 0 || colptr[n] != nnz) return ABFS_ERR_INVALID_ARG;
+    for (uint32_t v = 0; v < n; ++v)
+        if (colptr[v + 1] < colptr[v]) return ABFS_ERR_INVALID_ARG;
+    for (uint64_t e = 0; e < nnz; ++e)
+        if (rowidx[e] >= n) return ABFS_ERR_INVALID_ARG;
+    if (!directed) {
+        // symmetric pattern: every entry (i in column j) has its mirror
+        std::vector<uint32_t> rows(rowidx, rowidx + nnz);
+        for (uint32_t v = 0; v < n; ++v) std::sort(rows.begin() + colptr[v], rows.begin() + colptr[v + 1]);
+        for (uint32_t j = 0; j < n; ++j) {
+            for (uint32_t e = colptr[j]; e < colptr[j + 1]; ++e) {
+                const uint32_t i = rows[e];
+                if (!std::binary_search(rows.begin() + colptr[i], rows.begin() + colptr[i + 1], j))
+                    return ABFS_ERR_NOT_SYMMETRIC;
+            }
+        }
+    }
+    return ABFS_OK;
+}
+
+void free_workspace(Workspace& w) {
+    dev_free(w.base);
+    dev_free(w.d_done);
+    dev_free(w.d_beat);
+    dev_free(w.d_level);
+    dev_free(w.d_parent);
+    if (w.h_ctl) cudaFreeHost(w.h_ctl);
+    w = Workspace{};
+}
+
+Inst make_inst(const abfs_graph_s* g, char* base, const Layout& L, uint32_t src, int32_t* level,
+               int32_t* parent) {
+    Inst I;
+    std::memset(&I, 0, sizeof(I));
+    I.colptr = g->d_colptr;
+    I.rowidx = g->d_rowidx;
+    I.n = g->n;
+    I.src = src;
+    I.nwords = L.nwords;
+    I.hcap = L.hcap;
+    I.level = level;
+    I.parent = reinterpret_cast<uint32_t*>(parent);
+    for (int i = 0; i < 2; ++i) {
+        I.fq[i] = reinterpret_cast<uint32_t*>(base + L.fq[i]);
+        I.hq[i] = reinterpret_cast<uint2*>(base + L.hq[i]);
+        I.bm[i] = L.bm[i] ? reinterpret_cast<uint32_t*>(base + L.bm[i]) : nullptr;
+    }
+    if (L.y) I.y = reinterpret_cast<unsigned long long*>(base + L.y);
+    if (L.touched) I.touched = reinterpret_cast<uint32_t*>(base + L.touched);
+    for (uint32_t i = 0; i < L.ncopies; ++i) {
+        I.sbeg[i] = reinterpret_cast<uint32_t*>(base + L.sbeg[i]);
+        I.slen[i] = reinterpret_cast<uint32_t*>(base + L.slen[i]);
+        I.srows[i] = reinterpret_cast<uint32_t*>(base + L.srows[i]);
+    }
+    I.scap = L.scap;
+    I.ctl = reinterpret_cast<InstCtl*>(base + L.ctl);
+    return I;
+}
+
+// Ensures g->ws fits params p (reallocating after the previous use finished).
+int ensure_workspace(abfs_graph_s* g, const abfs_params& p) {
+    Workspace& w = g->ws;
+    if (w.base && same_layout(w.p, p)) {
+        w.p = p;
+        return ABFS_OK;
+    }
+    if (w.base) {
+        if (g->used) CK(cudaEventSynchronize(g->last_use));
+        free_workspace(w);
+    }
+    Layout L = layout_for(g->n, g->nnz, p);
+    int rc = dev_alloc((void**)&w.base, L.total);
+    if (rc) return rc;
+    rc = dev_alloc((void**)&w.d_done, 64);
+    if (!rc) rc = dev_alloc((void**)&w.d_beat, 64);
+    if (rc) {
+        free_workspace(w);
+        return rc;
+    }
+    if (cudaMallocHost((void**)&w.h_ctl, sizeof(InstCtl)) != cudaSuccess) {
+        cudaGetLastError();
+        free_workspace(w);
+        return ABFS_ERR_OOM;
+    }
+    w.L = L;
+    w.p = p;
+    w.d_inst = reinterpret_cast<Inst*>(w.base + L.inst);
+    Inst I = make_inst(g, w.base, L, 0, nullptr, nullptr);
+    cudaError_t e = cudaMemcpy(w.d_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_workspace(w);
+        return cuda_fail(e);
+    }
+    return ABFS_OK;
+}
+
+int grid_size(const abfs_graph_s* g, const abfs_params& p, uint32_t max_units_hint) {
+    int bps = 0;
+    if (engine_occupancy(p.mode, &bps) != cudaSuccess || bps < 1) bps = 1;
+    int per_sm = std::min<int>(bps, (int)p.ctas_per_sm);
+    int grid = per_sm * std::max(g->sms, 1);
+    (void)max_units_hint;
+    return std::max(grid, 1);
+}
+
+void fill_stats(const InstCtl& c, abfs_stats* st) {
+    std::memset(st, 0, sizeof(*st));
+    st->levels = c.levels;
+    st->reached = c.reached;
+    st->nnz_reached = c.nnz_reached;
+    st->entries_read = c.entries_read;
+    st->entries_unmasked = c.entries_unmasked;
+    st->claims = c.claims;
+    st->shrinks = c.shrinks;
+    st->wide_levels = c.wide_levels;
+    st->shrink_entries_read = c.shrink_read;
+    st->shrink_entries_kept = c.shrink_kept;
+    st->status = (c.status == kDone) ? 0u : (c.err ? c.err : (uint32_t)ABFS_ERR_DEVICE);
+}
+
+const abfs_params& pick_params(const abfs_graph_s* g, const abfs_params* params,
+                               abfs_params& tmp) {
+    if (params) return *params;
+    tmp = g->tuned ? g->tuned_params : default_params();
+    return tmp;
+}
+
+// Enqueues one search into g's workspace; caller holds g->mu.
+int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* parent,
+                   cudaStream_t s, const abfs_params& p) {
+    int rc = ensure_workspace(g, p);
+    if (rc) return rc;
+    Workspace& w = g->ws;
+    if (g->used) CK(cudaStreamWaitEvent(s, g->last_use, 0));
+    CK(launch_set_query(w.d_inst, source, level, reinterpret_cast<uint32_t*>(parent), s));
+    EngineArgs a;
+    a.insts = w.d_inst;
+    a.ninst = 1;
+    a.done_count = w.d_done;
+    a.heartbeat = w.d_beat;
+    a.p = engine_params(p);
+    CK(launch_init(a, g->n, s));
+    CK(launch_engine(a, grid_size(g, p, 0), s));
+    CK(cudaEventRecord(g->last_use, s));
+    g->used = true;
+    return ABFS_OK;
+}
+
+int finish_stats(abfs_graph_s* g, cudaStream_t s, abfs_stats* stats) {
+    Workspace& w = g->ws;
+    CK(cudaMemcpyAsync(w.h_ctl, w.base + w.L.ctl, sizeof(InstCtl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    fill_stats(*w.h_ctl, stats);
+    return stats->status;
+}
+
+}  // namespace
+
+extern "C" int abfs_default_params(abfs_params* p) {
+    if (!p) return ABFS_ERR_INVALID_ARG;
+    *p = default_params();
+    return ABFS_OK;
+}
+
+extern "C" int abfs_graph_create(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n,
+                                 uint64_t nnz, int directed, uint32_t flags, abfs_stream_t stream,
+                                 abfs_graph_t* out) {
+    if (!out || !colptr || (nnz && !rowidx) || n == 0) return ABFS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n >= (1u << 31) || nnz >= (1ull << 32)) return ABFS_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool on_dev = flags & ABFS_INPUT_ON_DEVICE;
+    std::vector<uint32_t> hc, hr;
+    if ((flags & ABFS_VALIDATE) && on_dev) {
+        hc.resize((size_t)n + 1);
+        hr.resize(nnz);
+        CK(cudaMemcpy(hc.data(), colptr, hc.size() * 4, cudaMemcpyDeviceToHost));
+        if (nnz) CK(cudaMemcpy(hr.data(), rowidx, nnz * 4, cudaMemcpyDeviceToHost));
+    }
+    if (flags & ABFS_VALIDATE) {
+        int rc = on_dev ? validate_host(hc.data(), hr.data(), n, nnz, directed)
+                        : validate_host(colptr, rowidx, n, nnz, directed);
+        if (rc) return rc;
+    }
+    abfs_graph_s* g = new (std::nothrow) abfs_graph_s();
+    if (!g) return ABFS_ERR_OOM;
+    g->n = n;
+    g->nnz = nnz;
+    g->directed = directed ? 1 : 0;
+    cudaGetDevice(&g->device);
+    cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device);
+    int rc = dev_alloc((void**)&g->d_colptr, ((size_t)n + 1) * 4);
+    if (!rc) rc = dev_alloc((void**)&g->d_rowidx, std::max<uint64_t>(nnz, 1) * 4);
+    if (rc) {
+        abfs_graph_destroy(g);
+        return rc;
+    }
+    const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(g->d_colptr, colptr, ((size_t)n + 1) * 4, kind, s);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(g->d_rowidx, rowidx, nnz * 4, kind, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->last_use, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        abfs_graph_destroy(g);
+        return cuda_fail(e);
+    }
+    *out = g;
+    return ABFS_OK;
+}
+
+extern "C" int abfs_graph_destroy(abfs_graph_t g) {
+    if (!g) return ABFS_ERR_INVALID_ARG;
+    if (g->used && g->last_use) cudaEventSynchronize(g->last_use);
+    free_workspace(g->ws);
+    dev_free(g->d_colptr);
+    dev_free(g->d_rowidx);
+    if (g->last_use) cudaEventDestroy(g->last_use);
+    delete g;
+    return ABFS_OK;
+}
+
+extern "C" int abfs_graph_info(abfs_graph_t g, uint32_t* n, uint64_t* nnz, int* directed) {
+    if (!g) return ABFS_ERR_INVALID_ARG;
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (directed) *directed = g->directed;
+    return ABFS_OK;
+}
+
+extern "C" int abfs_graph_footprint(abfs_graph_t g, const abfs_params* params, size_t* bytes) {
+    if (!g || !bytes) return ABFS_ERR_INVALID_ARG;
+    abfs_params tmp;
+    const abfs_params& p = pick_params(g, params, tmp);
+    int rc = check_params(p);
+    if (rc) return rc;
+    *bytes = layout_for(g->n, g->nnz, p).total;
+    return ABFS_OK;
+}
+
+extern "C" int abfs_run(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,
+                        abfs_stream_t stream, const abfs_params* params, abfs_stats* stats) {
+    if (!g || !level || !parent || source >= g->n) return ABFS_ERR_INVALID_ARG;
+    abfs_params tmp;
+    const abfs_params& p = pick_params(g, params, tmp);
+    int rc = check_params(p);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    rc = enqueue_single(g, source, level, parent, s, p);
+    if (rc) return rc;
+    if (stats) return finish_stats(g, s, stats);
+    return ABFS_OK;
+}
+
+extern "C" int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_host,
+                             int32_t* parent_host, abfs_stream_t stream, const abfs_params* params,
+                             abfs_stats* stats) {
+    if (!g || !level_host || !parent_host || source >= g->n) return ABFS_ERR_INVALID_ARG;
+    abfs_params tmp;
+    const abfs_params& p = pick_params(g, params, tmp);
+    int rc = check_params(p);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    Workspace& w = g->ws;
+    if (!w.d_level) {
+        rc = dev_alloc((void**)&w.d_level, (size_t)g->n * 4);
+        if (!rc) rc = dev_alloc((void**)&w.d_parent, (size_t)g->n * 4);
+        if (rc) return rc;
+    }
+    rc = enqueue_single(g, source, w.d_level, w.d_parent, s, p);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(level_host, w.d_level, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(parent_host, w.d_parent, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+    if (stats) return finish_stats(g, s, stats);
+    CK(cudaStreamSynchronize(s));
+    return ABFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+
+struct abfs_batch_s {
+    std::vector<abfs_graph_t> graphs;
+    uint32_t count = 0;
+    abfs_params p{};
+    char* ws = nullptr;          // all per-instance workspaces
+    Inst* d_insts = nullptr;
+    uint32_t* d_done = nullptr;
+    unsigned long long* d_beat = nullptr;
+    std::vector<size_t> ctl_off; // offset of each InstCtl in ws
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    InstCtl* h_ctl = nullptr;    // pinned, count entries
+};
+
+extern "C" int abfs_batch_destroy(abfs_batch_t b) {
+    if (!b) return ABFS_ERR_INVALID_ARG;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    dev_free(b->ws);
+    dev_free(b->d_insts);
+    dev_free(b->d_done);
+    dev_free(b->d_beat);
+    if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    delete b;
+    return ABFS_OK;
+}
+
+extern "C" int abfs_batch_create(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
+                                 int32_t* const* level, int32_t* const* parent,
+                                 const abfs_params* params, abfs_stream_t stream,
+                                 abfs_batch_t* out) {
+    if (!g || !sources || !level || !parent || !out || count == 0) return ABFS_ERR_INVALID_ARG;
+    *out = nullptr;
+    abfs_params tmp;
+    const abfs_params& p = pick_params(g[0], params, tmp);
+    int rc = check_params(p);
+    if (rc) return rc;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (!g[i] || !level[i] || !parent[i] || sources[i] >= g[i]->n) return ABFS_ERR_INVALID_ARG;
+        if (g[i]->device != g[0]->device) return ABFS_ERR_INVALID_ARG;
+    }
+    abfs_batch_s* b = new (std::nothrow) abfs_batch_s();
+    if (!b) return ABFS_ERR_OOM;
+    b->graphs.assign(g, g + count);
+    b->count = count;
+    b->p = p;
+    std::vector<Layout> L(count);
+    std::vector<size_t> base(count);
+    size_t total = 0;
+    uint32_t max_n = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        L[i] = layout_for(g[i]->n, g[i]->nnz, p);
+        base[i] = total;
+        total = align_up(total + L[i].total, 256);
+        max_n = std::max(max_n, g[i]->n);
+    }
+    rc = dev_alloc((void**)&b->ws, total);
+    if (!rc) rc = dev_alloc((void**)&b->d_insts, sizeof(Inst) * count);
+    if (!rc) rc = dev_alloc((void**)&b->d_done, 64);
+    if (!rc) rc = dev_alloc((void**)&b->d_beat, 64);
+    if (rc) {
+        abfs_batch_destroy(b);
+        return rc;
+    }
+    if (cudaMallocHost((void**)&b->h_ctl, sizeof(InstCtl) * count) != cudaSuccess) {
+        cudaGetLastError();
+        abfs_batch_destroy(b);
+        return ABFS_ERR_OOM;
+    }
+    std::vector<Inst> hI(count);
+    b->ctl_off.resize(count);
+    for (uint32_t i = 0; i < count; ++i) {
+        hI[i] = make_inst(g[i], b->ws + base[i], L[i], sources[i], level[i], parent[i]);
+        b->ctl_off[i] = base[i] + L[i].ctl;
+    }
+    cudaError_t e = cudaMemcpy(b->d_insts, hI.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        abfs_batch_destroy(b);
+        return cuda_fail(e);
+    }
+    // capture initialisation + the persistent launch in a CUDA graph
+    cudaStream_t cap;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        abfs_batch_destroy(b);
+        return cuda_fail(e);
+    }
+    EngineArgs a;
+    a.insts = b->d_insts;
+    a.ninst = count;
+    a.done_count = b->d_done;
+    a.heartbeat = b->d_beat;
+    a.p = engine_params(p);
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = launch_init(a, max_n, cap);
+        cudaError_t e2 = launch_engine(a, grid_size(g[0], p, 0), cap);
+        e = cudaStreamEndCapture(cap, &b->graph);
+        if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        abfs_batch_destroy(b);
+        return cuda_fail(e);
+    }
+    (void)stream;
+    *out = b;
+    return ABFS_OK;
+}
+
+extern "C" int abfs_batch_launch(abfs_batch_t b, abfs_stream_t stream) {
+    if (!b) return ABFS_ERR_INVALID_ARG;
+    CK(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    return ABFS_OK;
+}
+
+extern "C" int abfs_batch_status(abfs_batch_t b, abfs_stream_t stream, int32_t* status) {
+    if (!b || !status) return ABFS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (uint32_t i = 0; i < b->count; ++i)
+        CK(cudaMemcpyAsync(b->h_ctl + i, b->ws + b->ctl_off[i], sizeof(InstCtl),
+                           cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int worst = ABFS_OK;
+    for (uint32_t i = 0; i < b->count; ++i) {
+        const InstCtl& c = b->h_ctl[i];
+        status[i] = (c.status == kDone) ? ABFS_OK : (c.err ? (int)c.err : ABFS_ERR_DEVICE);
+        if (status[i] && !worst) worst = status[i];
+    }
+    return worst;
+}
+
+extern "C" int abfs_run_batch(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
+                              int32_t* const* level, int32_t* const* parent, abfs_stream_t stream,
+                              const abfs_params* params, int32_t* status_per_query) {
+    abfs_batch_t b = nullptr;
+    int rc = abfs_batch_create(g, sources, count, level, parent, params, stream, &b);
+    if (rc) return rc;
+    rc = abfs_batch_launch(b, stream);
+    std::vector<int32_t> st(count);
+    int rc2 = abfs_batch_status(b, stream, st.data());
+    if (status_per_query) std::copy(st.begin(), st.end(), status_per_query);
+    abfs_batch_destroy(b);
+    return rc ? rc : rc2;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+
+namespace {
+
+std::string size_class(const abfs_graph_s* g) {
+    const int lgn = (int)std::ceil(std::log2((double)g->n + 1));
+    const double deg = (double)g->nnz / std::max<uint32_t>(g->n, 1);
+    const int lgd = (int)std::floor(std::log2(deg + 1.0));
+    std::ostringstream o;
+    o << "n2^" << lgn << "_d2^" << lgd << (g->directed ? "_dir" : "_und");
+    return o.str();
+}
+
+std::string gpu_name(int dev) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    std::string s = prop.name;
+    for (char& c : s)
+        if (c == ' ' || c == '"') c = '_';
+    return s;
+}
+
+std::string params_json(const abfs_params& p) {
+    std::ostringstream o;
+    o << "\"mode\":" << p.mode << ",\"tile\":" << p.tile << ",\"heavy_degree\":" << p.heavy_degree
+      << ",\"chunk\":" << p.chunk << ",\"narrow_max\":" << p.narrow_max
+      << ",\"ctas_per_sm\":" << p.ctas_per_sm << ",\"shrink_theta\":" << p.shrink_theta
+      << ",\"shrink_max\":" << p.shrink_max;
+    return o.str();
+}
+
+bool json_num(const std::string& line, const std::string& key, double* v) {
+    const std::string k = "\"" + key + "\":";
+    size_t at = line.find(k);
+    if (at == std::string::npos) return false;
+    *v = std::strtod(line.c_str() + at + k.size(), nullptr);
+    return true;
+}
+
+bool json_str(const std::string& line, const std::string& key, std::string* v) {
+    const std::string k = "\"" + key + "\":\"";
+    size_t at = line.find(k);
+    if (at == std::string::npos) return false;
+    size_t end = line.find('"', at + k.size());
+    if (end == std::string::npos) return false;
+    *v = line.substr(at + k.size(), end - at - k.size());
+    return true;
+}
+
+}  // namespace
+
+extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count, uint32_t mode,
+                         const char* cache_path, abfs_stream_t stream, abfs_params* best,
+                         float* best_ms) {
+    if (!g || !sources || count == 0 || mode > ABFS_MODE_PLAIN) return ABFS_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < count; ++i)
+        if (sources[i] >= g->n) return ABFS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const std::string key_gpu = gpu_name(g->device);
+    const std::string key_cls = size_class(g);
+    // cache lookup: JSON lines {"gpu":..,"sms":..,"mode":..,"class":..,<params>,"ms":..}
+    if (cache_path) {
+        std::ifstream in(cache_path);
+        std::string line, found;
+        while (std::getline(in, line)) {
+            std::string gpu, cls;
+            double sms = 0, md = -1;
+            if (json_str(line, "gpu", &gpu) && json_str(line, "class", &cls) &&
+                json_num(line, "sms", &sms) && json_num(line, "mode", &md) && gpu == key_gpu &&
+                cls == key_cls && (int)sms == g->sms && (uint32_t)md == mode)
+                found = line;
+        }
+        if (!found.empty()) {
+            abfs_params p = default_params();
+            double v;
+            if (json_num(found, "tile", &v)) p.tile = (uint32_t)v;
+            if (json_num(found, "heavy_degree", &v)) p.heavy_degree = (uint32_t)v;
+            if (json_num(found, "chunk", &v)) p.chunk = (uint32_t)v;
+            if (json_num(found, "narrow_max", &v)) p.narrow_max = (uint32_t)v;
+            if (json_num(found, "ctas_per_sm", &v)) p.ctas_per_sm = (uint32_t)v;
+            if (json_num(found, "shrink_theta", &v)) p.shrink_theta = (float)v;
+            if (json_num(found, "shrink_max", &v)) p.shrink_max = (uint32_t)v;
+            p.mode = mode;
+            if (check_params(p) == ABFS_OK) {
+                std::lock_guard<std::mutex> lk(g->mu);
+                g->tuned = true;
+                g->tuned_params = p;
+                if (best) *best = p;
+                if (best_ms && json_num(found, "ms", &v)) *best_ms = (float)v;
+                return ABFS_OK;
+            }
+        }
+    }
+    // candidate sets
+    std::vector<abfs_params> cands;
+    const uint32_t tiles[] = {512, 1024, 2048};
+    const uint32_t chunks[] = {2048, 8192};
+    const uint32_t narrows[] = {0, 256, 1024};
+    const uint32_t ctas[] = {1, 2};
+    for (uint32_t t : tiles)
+        for (uint32_t c : chunks)
+            for (uint32_t nm : narrows)
+                for (uint32_t cp : ctas) {
+                    abfs_params p = default_params();
+                    p.mode = mode;
+                    p.tile = t;
+                    p.chunk = c;
+                    p.heavy_degree = c;
+                    p.narrow_max = std::min(nm, t);
+                    p.ctas_per_sm = cp;
+                    cands.push_back(p);
+                }
+    if (mode == ABFS_MODE_SUBMATRIX) {
+        const float thetas[] = {0.5f, 0.8f, 0.95f};
+        for (float th : thetas) {
+            abfs_params p = default_params();
+            p.mode = mode;
+            p.shrink_theta = th;
+            p.shrink_max = 1;
+            cands.push_back(p);
+        }
+    }
+    int32_t *d_level = nullptr, *d_parent = nullptr;
+    int rc = dev_alloc((void**)&d_level, (size_t)g->n * 4);
+    if (!rc) rc = dev_alloc((void**)&d_parent, (size_t)g->n * 4);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = ABFS_ERR_CUDA;
+    float best_time = INFINITY;
+    abfs_params best_p = default_params();
+    best_p.mode = mode;
+    for (size_t ci = 0; ci < cands.size() && !rc; ++ci) {
+        const abfs_params& p = cands[ci];
+        std::lock_guard<std::mutex> lk(g->mu);
+        // warm-up (also allocates the workspace)
+        rc = enqueue_single(g, sources[0], d_level, d_parent, s, p);
+        if (rc) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { rc = ABFS_ERR_CUDA; break; }
+        for (uint32_t i = 0; i < count && !rc; ++i)
+            rc = enqueue_single(g, sources[i], d_level, d_parent, s, p);
+        if (rc) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = ABFS_ERR_CUDA;
+            break;
+        }
+        abfs_stats st;
+        rc = finish_stats(g, s, &st);
+        if (rc) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= count;
+        if (ms < best_time) {
+            best_time = ms;
+            best_p = p;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(d_level);
+    dev_free(d_parent);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        g->tuned = true;
+        g->tuned_params = best_p;
+    }
+    if (best) *best = best_p;
+    if (best_ms) *best_ms = best_time;
+    if (cache_path) {
+        std::ofstream o(cache_path, std::ios::app);
+        o << "{\"gpu\":\"" << key_gpu << "\",\"sms\":" << g->sms << ",\"class\":\"" << key_cls
+          << "\"," << params_json(best_p) << ",\"ms\":" << best_time << "}\n";
+    }
+    return ABFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// allocator hook
+// ---------------------------------------------------------------------------
+
+extern "C" int abfs_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*),
+                                  void* ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) return ABFS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.free = free_fn;
+    g_alloc.ctx = ctx;
+    return ABFS_OK;
+}
+
+extern "C" const char* abfs_last_cuda_error(void) { return g_last_cuda_error.c_str(); }

@@ -1,0 +1,305 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Levels and min-index parents are integers: the bar is bit-exact equality,
+element by element, for every mode, parameter set and batch mix.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1906_03113_gb300 as abfs  # noqa: E402
+
+SUB = abfs.MODE_SUBMATRIX
+PLAIN = abfs.MODE_PLAIN
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    abfs.build()
+    abfs.load()
+    torch.cuda.set_device(0)
+
+
+def _check(g, src, level, parent, ctx=""):
+    lev_o, par_o = oracle.bfs(g, src)
+    lev = level.cpu().numpy() if hasattr(level, "cpu") else level
+    par = parent.cpu().numpy() if hasattr(parent, "cpu") else parent
+    bad = np.nonzero(lev != lev_o)[0]
+    assert bad.size == 0, f"{ctx}: level mismatch at {bad[:8]} ({lev[bad[:8]]} vs {lev_o[bad[:8]]})"
+    bad = np.nonzero(par != par_o)[0]
+    assert bad.size == 0, f"{ctx}: parent mismatch at {bad[:8]} ({par[bad[:8]]} vs {par_o[bad[:8]]})"
+    return lev_o
+
+
+def _params(mode=SUB, **kw):
+    return abfs.default_params(mode=mode, **kw)
+
+
+MODES = [
+    ("sub", dict(mode=SUB)),
+    ("plain", dict(mode=PLAIN)),
+    ("sub_shrink", dict(mode=SUB, shrink_theta=0.3, shrink_max=3)),
+    ("sub_small_tiles", dict(mode=SUB, tile=32, narrow_max=0, heavy_degree=128, chunk=128)),
+    ("plain_small_tiles", dict(mode=PLAIN, tile=64, narrow_max=32, heavy_degree=256, chunk=128)),
+    ("sub_narrow_all", dict(mode=SUB, tile=2048, narrow_max=2048)),
+    ("sub_wide_all", dict(mode=SUB, tile=256, narrow_max=0, ctas_per_sm=1)),
+    ("sub_shrink_every", dict(mode=SUB, tile=128, narrow_max=0, shrink_theta=0.05, shrink_max=20,
+                              heavy_degree=256, chunk=128)),
+]
+
+
+def _small_graphs():
+    star_leaves = 20000
+    return {
+        "fig1_path": synth.from_arcs(5, [0, 1, 2, 2], [3, 4, 3, 4], directed=False),
+        "er_2000": synth.er(2000, 3.0, seed=2),
+        "er_2_16": synth.er_2_16(),
+        "rmat_14": synth.rmat(14, 16.0, seed=3),
+        "grid_100x37": synth.grid(100, 37),
+        "grid_1x1000": synth.grid(1, 1000),
+        "rgg_2_15": synth.rgg_knn(1 << 15, 4, seed=4),
+        "star": synth.from_arcs(star_leaves + 1, [0] * star_leaves, list(range(1, star_leaves + 1)),
+                                directed=False),
+        "path_3000": synth.from_arcs(3000, list(range(2999)), list(range(1, 3000)), directed=False),
+        "complete_200": synth.from_arcs(200, [i for i in range(200) for j in range(i + 1, 200)],
+                                        [j for i in range(200) for j in range(i + 1, 200)], directed=False),
+        "dicycle_777": synth.from_arcs(777, list(range(777)), [(i + 1) % 777 for i in range(777)],
+                                       directed=True),
+        "two_components": synth.from_arcs(100, list(range(49)) + list(range(50, 99)),
+                                          list(range(1, 50)) + list(range(51, 100)), directed=False),
+        "no_edges": synth.from_arcs(77, [], [], directed=False),
+    }
+
+
+@pytest.fixture(scope="module")
+def small():
+    gs = _small_graphs()
+    dev = {k: abfs.graph_create(g.colptr, g.rowidx, directed=g.directed, validate=True)
+           for k, g in gs.items()}
+    yield gs, dev
+    for G in dev.values():
+        G.destroy()
+
+
+def _sources(g):
+    deg = g.degrees()
+    cand = [0, g.n - 1, int(np.argmax(deg)), g.n // 2]
+    nz = np.nonzero(deg > 0)[0]
+    if nz.size:
+        cand.append(int(nz[len(nz) // 3]))
+    return sorted(set(int(c) for c in cand))
+
+
+@pytest.mark.parametrize("mode_name,kw", MODES, ids=[m[0] for m in MODES])
+def test_small_graphs_all_modes(small, mode_name, kw):
+    gs, dev = small
+    p = _params(**kw)
+    for name, g in gs.items():
+        for s in _sources(g):
+            level, parent, st = abfs.run(dev[name], s, params=p, stats=True)
+            torch.cuda.synchronize()
+            assert st["status"] == 0, (name, s, st)
+            lev_o = _check(g, s, level, parent, f"{mode_name}/{name}/src{s}")
+            reached = lev_o >= 0
+            assert st["reached"] == int(reached.sum()), (name, s, st)
+            assert st["levels"] == int(lev_o.max()) + 1, (name, s, st)
+            nnz_c = int(g.degrees()[reached].sum())
+            assert st["nnz_reached"] == nnz_c, (name, s, st)
+            if kw.get("mode") == PLAIN:
+                assert st["entries_read"] == nnz_c and st["entries_unmasked"] == nnz_c
+            elif not kw.get("shrink_theta"):
+                # each reached column is read exactly once (Claim 1)
+                assert st["entries_read"] == nnz_c, (name, s, st)
+                assert st["entries_unmasked"] <= nnz_c
+            else:
+                assert st["entries_read"] <= nnz_c
+
+
+def test_fig1_frontiers_through_gpu(small):
+    gs, dev = small
+    level, parent = abfs.run(dev["fig1_path"], 1)
+    assert level.cpu().tolist() == [4, 0, 2, 3, 1]
+    assert parent.cpu().tolist() == [3, 1, 4, 2, 1]
+
+
+def test_invalid_source_rejected(small):
+    gs, dev = small
+    with pytest.raises(abfs.AbfsError) as ei:
+        abfs.run(dev["er_2000"], 2000)
+    assert ei.value.status == 1
+
+
+def test_run_host_matches(small):
+    gs, dev = small
+    g = gs["rmat_14"]
+    s = _sources(g)[-1]
+    lev_h, par_h = abfs.run_host(dev["rmat_14"], s)
+    _check(g, s, lev_h, par_h, "run_host")
+
+
+def test_repeated_runs_identical(small):
+    gs, dev = small
+    g = gs["rmat_14"]
+    s = int(np.argmax(g.degrees()))
+    ref = None
+    for _ in range(5):
+        level, parent = abfs.run(dev["rmat_14"], s)
+        cur = (level.cpu().numpy().copy(), parent.cpu().numpy().copy())
+        if ref is not None:
+            assert np.array_equal(ref[0], cur[0]) and np.array_equal(ref[1], cur[1])
+        ref = cur
+
+
+def test_exhaustive_tiny_graphs_in_one_batch():
+    """Every directed graph on 4 vertices and every undirected graph on 5,
+    from every source, as instances of persistent batch launches."""
+    jobs = []
+    for n, directed in ((4, True), (5, False)):
+        pairs = ([(i, j) for i in range(n) for j in range(n) if i != j] if directed
+                 else [(i, j) for i in range(n) for j in range(i + 1, n)])
+        for mask in range(1 << len(pairs)):
+            arcs = [pairs[b] for b in range(len(pairs)) if mask >> b & 1]
+            g = synth.from_arcs(n, [a for a, _ in arcs], [b for _, b in arcs], directed=directed)
+            jobs.append(g)
+    for mode in (SUB, PLAIN):
+        dev = [abfs.graph_create(g.colptr, g.rowidx, directed=g.directed) for g in jobs]
+        graphs, srcs, hosts = [], [], []
+        for G, g in zip(dev, jobs):
+            for s in range(g.n):
+                graphs.append(G)
+                srcs.append(s)
+                hosts.append(g)
+        levels, parents, st = abfs.run_batch(graphs, srcs, params=_params(mode=mode, tile=32,
+                                                                           narrow_max=32))
+        torch.cuda.synchronize()
+        assert all(x == 0 for x in st)
+        for g, s, L, P in zip(hosts, srcs, levels, parents):
+            _check(g, s, L, P, f"tiny mode{mode}")
+        for G in dev:
+            G.destroy()
+
+
+def test_batch_alone_equals_mix(small):
+    gs, dev = small
+    names = ["er_2_16", "rmat_14", "grid_100x37", "rgg_2_15", "star", "path_3000", "no_edges"]
+    graphs, srcs, hosts = [], [], []
+    for nm in names:
+        for s in _sources(gs[nm])[:3]:
+            graphs.append(dev[nm])
+            srcs.append(s)
+            hosts.append(gs[nm])
+    for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, shrink_theta=0.4, shrink_max=2)):
+        p = _params(**kw)
+        levels, parents, st = abfs.run_batch(graphs, srcs, params=p)
+        torch.cuda.synchronize()
+        assert all(x == 0 for x in st), st
+        for G, g, s, L, P in zip(graphs, hosts, srcs, levels, parents):
+            la, pa = abfs.run(G, s, params=p)
+            assert torch.equal(la, L) and torch.equal(pa, P), (g.name, s, kw)
+            _check(g, s, L, P, f"batch {kw}")
+
+
+def test_batch_plan_replays(small):
+    gs, dev = small
+    graphs = [dev["rmat_14"], dev["er_2_16"], dev["grid_100x37"]]
+    hosts = [gs["rmat_14"], gs["er_2_16"], gs["grid_100x37"]]
+    srcs = [int(np.argmax(h.degrees())) for h in hosts]
+    plan = abfs.BatchPlan(graphs, srcs)
+    for rep in range(3):
+        for L in plan.levels:
+            L.fill_(7)
+        plan.launch()
+        assert plan.status() == [0, 0, 0]
+        for g, s, L, P in zip(hosts, srcs, plan.levels, plan.parents):
+            _check(g, s, L, P, f"plan replay {rep}")
+    plan.destroy()
+
+
+def test_tune_keeps_results(small, tmp_path):
+    gs, dev = small
+    g = gs["rmat_14"]
+    srcs = _sources(g)[:2]
+    cache = str(tmp_path / "tune.json")
+    best, ms = abfs.tune(dev["rmat_14"], srcs, SUB, cache)
+    assert ms > 0 and best.tile >= 32
+    best2, ms2 = abfs.tune(dev["rmat_14"], srcs, SUB, cache)   # from the cache
+    assert best2.as_dict() == best.as_dict()
+    level, parent = abfs.run(dev["rmat_14"], srcs[0])          # uses the tuned params
+    _check(g, srcs[0], level, parent, "tuned")
+
+
+def test_device_inputs_and_validation():
+    g = synth.rmat(12, 8.0, seed=5)
+    cp = torch.from_numpy(g.colptr.view(np.int32)).cuda()
+    ri = torch.from_numpy(g.rowidx.view(np.int32)).cuda()
+    G = abfs.graph_create(cp, ri, directed=False, validate=True)
+    s = int(np.argmax(g.degrees()))
+    level, parent = abfs.run(G, s)
+    _check(g, s, level, parent, "device input")
+    G.destroy()
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def rmat22():
+    g = synth.rmat_22()
+    G = abfs.graph_create(g.colptr, g.rowidx, directed=False)
+    yield g, G
+    G.destroy()
+
+
+def test_rmat22_16_sources(rmat22):
+    g, G = rmat22
+    srcs = synth.sources_with_degree(g, 16, seed=1)
+    for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, shrink_theta=0.6, shrink_max=1)):
+        p = _params(**kw)
+        for s in srcs[: (16 if kw == dict(mode=SUB) else 4)]:
+            level, parent, st = abfs.run(G, int(s), params=p, stats=True)
+            assert st["status"] == 0
+            _check(g, int(s), level, parent, f"rmat22 {kw} src{s}")
+
+
+def test_rmat22_batch_64_sources(rmat22):
+    g, G = rmat22
+    srcs = synth.sources_with_degree(g, 64, seed=2)
+    levels, parents, st = abfs.run_batch([G] * 64, srcs)
+    torch.cuda.synchronize()
+    assert all(x == 0 for x in st)
+    for i in (0, 17, 63):
+        _check(g, int(srcs[i]), levels[i], parents[i], f"rmat22 batch {i}")
+
+
+def test_grid_4096():
+    g = synth.grid_4096()
+    G = abfs.graph_create(g.colptr, g.rowidx, directed=False)
+    for mode in (SUB, PLAIN):
+        level, parent, st = abfs.run(G, 0, params=_params(mode=mode), stats=True)
+        assert st["status"] == 0 and st["levels"] == 8191
+        lev = level.cpu().numpy()
+        par = parent.cpu().numpy()
+        v = np.arange(g.n)
+        r, c = v // 4096, v % 4096
+        assert np.array_equal(lev, r + c)                     # Manhattan distance
+        exp = np.where(r > 0, v - 4096, v - 1)
+        exp[0] = 0
+        assert np.array_equal(par, exp)
+    G.destroy()
+
+
+def test_rgg_2_22():
+    g = synth.rgg_2_22()
+    G = abfs.graph_create(g.colptr, g.rowidx, directed=True)
+    for mode in (SUB, PLAIN):
+        level, parent = abfs.run(G, 0, params=_params(mode=mode))
+        _check(g, 0, level, parent, f"rgg22 mode{mode}")
+    G.destroy()
