@@ -1,0 +1,400 @@
+"""Benchmark of the algebraic BFS on GB300.
+
+Default workload: undirected R-MAT scale 22 (edge factor 16, a/b/c/d =
+.57/.19/.19/.05, permuted labels), 16 sources drawn uniformly from the
+vertices of degree >= 1.  One step = one BFS from each of the 16 sources
+through the C-ABI (abfs_run), inputs resident in HBM.  The metric is GTEPS:
+edges of the reached component (m_c = nnz_c / 2 for undirected graphs) over
+device time.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank runs the same
+workload on its own GPU (independent replicas; BFS queries shard with no
+exchange), value = all ranks' edges / max-over-ranks time.
+
+--impl reference runs the CPU oracle (sorted-frontier queue BFS, one host
+core) on the same workload, bounded to a few minutes.
+--workload selects one of the other workloads (er16, grid4096, rgg22,
+batch512) for measurement runs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def make_workload(name: str):
+    if name == "rmat22":
+        g = synth.rmat_22()
+        srcs = synth.sources_with_degree(g, 16, seed=1)
+        desc = ("rmat22_16src", "R-MAT scale 22, edge factor 16, a/b/c/d=.57/.19/.19/.05, permuted, "
+                "undirected, 16 sources from degree>=1 (seed 1)")
+    elif name == "er16":
+        g = synth.er_2_16()
+        srcs = np.array([0], dtype=np.uint32)
+        desc = ("er16_src0", "Erdos-Renyi G(n,p) n=2^16 p=8/(n-1) undirected, source 0 (seed 1)")
+    elif name == "grid4096":
+        g = synth.grid_4096()
+        srcs = np.array([0], dtype=np.uint32)
+        desc = ("grid4096_src0", "4096x4096 4-neighbour grid undirected, source 0")
+    elif name == "rgg22":
+        g = synth.rgg_2_22()
+        srcs = np.array([0], dtype=np.uint32)
+        desc = ("rgg22_src0", "directed 4-NN random geometric graph n=2^22, source 0 (seed 1)")
+    else:
+        raise ValueError(name)
+    return g, srcs, desc
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    g, srcs, (wname, wdesc) = make_workload(args.workload)
+    deg = g.degrees()
+    directed = g.directed
+    budget_s = 150.0
+    # warm-up step (one source), also sizes the bounded sample
+    t0 = time.perf_counter()
+    lev, _ = oracle.bfs(g, int(srcs[0]))
+    t_one = time.perf_counter() - t0
+    steps = max(1, min(args.steps, int(budget_s / max(t_one, 1e-3))))
+    edges, total = 0, 0.0
+    for k in range(steps):
+        s = int(srcs[k % len(srcs)])
+        t0 = time.perf_counter()
+        lev, _ = oracle.bfs(g, s)
+        total += time.perf_counter() - t0
+        nnz_c = int(deg[lev >= 0].sum())
+        edges += nnz_c if directed else nnz_c // 2
+    gteps = edges / total / 1e9
+    line = {
+        "impl": "reference", "metric": "GTEPS", "value": gteps, "unit": "GTEPS", "n_gpus": ws,
+        "steps": steps, "steps_requested": args.steps, "warmup": 1,
+        "ms_per_step": total / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wname, "graph": wdesc, "step": "one BFS from one source (rotating)"},
+        "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} single-source BFS of the workload, sources rotating"},
+        "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(g, srcs, max_seconds=20.0):
+    """The oracle (sorted-frontier queue BFS, one thread) on a bounded sample."""
+    import oracle
+    deg = g.degrees()
+    edges, total, used = 0, 0.0, 0
+    for s in srcs:
+        t0 = time.perf_counter()
+        lev, _ = oracle.bfs(g, int(s))
+        total += time.perf_counter() - t0
+        used += 1
+        nnz_c = int(deg[lev >= 0].sum())
+        edges += nnz_c if g.directed else nnz_c // 2
+        if total > max_seconds:
+            break
+    return {"value": edges / total / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{used} of the {len(srcs)} sources, one BFS each, on one host core "
+                      f"({total:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22",
+                    choices=["rmat22", "er16", "grid4096", "rgg22"])
+    ap.add_argument("--mode", default="sub", choices=["sub", "plain"])
+    ap.add_argument("--shrink", type=float, default=0.0)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import paper_1906_03113_gb300 as abfs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    abfs.load()
+
+    g, srcs, (wname, wdesc) = make_workload(args.workload)
+    G = abfs.graph_create(g.colptr, g.rowidx, directed=g.directed)
+    mode = abfs.MODE_PLAIN if args.mode == "plain" else abfs.MODE_SUBMATRIX
+    params = abfs.default_params(mode=mode)
+    if args.shrink > 0:
+        params.shrink_theta = args.shrink
+        params.shrink_max = 1
+    stream = torch.cuda.current_stream()
+    n = g.n
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    # per-source counters (outside the timed region)
+    per_src = []
+    for s in srcs:
+        _, _, st = abfs.run(G, int(s), level, parent, stream, params, stats=True)
+        assert st["status"] == 0, st
+        per_src.append(st)
+    nnz_c = np.array([st["nnz_reached"] for st in per_src], dtype=np.float64)
+    m_c = nnz_c if g.directed else nnz_c / 2.0
+    e_adj = np.array([st["entries_unmasked"] for st in per_src], dtype=np.float64)
+    n_c = np.array([st["reached"] for st in per_src], dtype=np.float64)
+    if mode == abfs.MODE_PLAIN:
+        # the comparator multiplies every entry; E_adj comes from a submatrix run
+        e_adj = []
+        for s in srcs:
+            _, _, st = abfs.run(G, int(s), level, parent, stream, abfs.default_params(), stats=True)
+            e_adj.append(st["entries_unmasked"])
+        e_adj = np.array(e_adj, dtype=np.float64)
+    b_alg = 4.0 * e_adj + 24.0 * n_c           # algorithmic bytes per BFS
+    b_cols = 4.0 * nnz_c + 24.0 * n_c          # bytes with every reached column read once
+
+    def one_step():
+        for s in srcs:
+            abfs.run(G, int(s), level, parent, stream, params)
+
+    for _ in range(max(args.warmup, 3)):
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    nsrc = len(srcs)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * nsrc + 1)]
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    ev[0].record(stream)
+    i = 0
+    for _ in range(args.steps):
+        for s in srcs:
+            abfs.run(G, int(s), level, parent, stream, params)
+            i += 1
+            ev[i].record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(stop)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    per_bfs_ms = np.array([ev[j].elapsed_time(ev[j + 1]) for j in range(args.steps * nsrc)])
+    per_bfs_ms = per_bfs_ms.reshape(args.steps, nsrc).mean(axis=0)  # mean per source
+    edges_per_step = float(m_c.sum())
+    value = edges_per_step * args.steps * ws / (total_ms * 1e-3) / 1e9
+
+    hbm, peak_kind = _peaks()
+    mean_t = float(per_bfs_ms.mean()) * 1e-3
+    achieved = float(b_alg.mean()) / mean_t / 1e9
+    line = {
+        "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": wname, "graph": wdesc, "n": n, "nnz": g.nnz,
+                   "sources": nsrc, "mode": args.mode, "shrink_theta": args.shrink,
+                   "step": f"{nsrc} single-source BFS via abfs_run",
+                   "l2": f"inputs larger than L2: rowidx {g.nnz * 4 / 1e6:.0f} MB",
+                   "parallelism": f"replicas x{ws}", "edges": "m_c = nnz_c/2" if not g.directed
+                   else "m_c = nnz_c"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                     "kernel": "engine_kernel<0> (one launch per BFS, with 3 small init kernels)",
+                     "bytes_per_bfs": float(b_alg.mean()),
+                     "bytes_formula": "4*E_adj + 24*n_c",
+                     "full_column_gbs": float(b_cols.mean()) / mean_t / 1e9},
+        "gpu_launches": 4 * nsrc * args.steps,
+        "clocks": clk,
+        "per_bfs_ms": float(per_bfs_ms.mean()),
+        "reached_mean": float(n_c.mean()), "nnz_c_mean": float(nnz_c.mean()),
+        "e_adj_mean": float(e_adj.mean()),
+        "gteps_2m": value * (1.0 if g.directed else 2.0),
+    }
+
+    # end to end through host buffers (abfs_run_host)
+    lev_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    par_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 10))
+    abfs.run_host(G, int(srcs[0]), lev_h, par_h, stream, params)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for s in srcs:
+            abfs.run_host(G, int(s), lev_h, par_h, stream, params)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    line["e2e"] = {"value": edges_per_step * e2e_steps * ws / e2e_s / 1e9, "unit": "GTEPS",
+                   "h2d_bytes_per_step": 4 * nsrc, "d2h_bytes_per_step": 8 * n * nsrc,
+                   "steps": e2e_steps, "api": "abfs_run_host into pinned host buffers"}
+
+    if not args.no_extras and ws == 1:
+        # comparator on the same GPU: plain masked SpMSpV (multiply, then mask)
+        pp = abfs.default_params(mode=abfs.MODE_PLAIN)
+        for s in srcs:
+            abfs.run(G, int(s), level, parent, stream, pp)
+        torch.cuda.synchronize()
+        c_steps = max(1, args.steps // 4)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(c_steps):
+            for s in srcs:
+                abfs.run(G, int(s), level, parent, stream, pp)
+        b.record(stream)
+        torch.cuda.synchronize()
+        cms = a.elapsed_time(b)
+        cval = edges_per_step * c_steps / (cms * 1e-3) / 1e9
+        line["comparator"] = {"name": "plain masked SpMSpV (same engine, multiply then mask)",
+                              "value": cval, "unit": "GTEPS", "speedup_of_ours": value / cval}
+        # batched: 64 sources in one persistent launch (CUDA graph replay)
+        if args.workload == "rmat22":
+            bs = synth.sources_with_degree(g, 64, seed=2)
+            plan = abfs.BatchPlan([G] * 64, bs)
+            plan.launch()
+            torch.cuda.synchronize()
+            assert all(x == 0 for x in plan.status())
+            bm_c = []
+            for s in bs:
+                _, _, st = abfs.run(G, int(s), level, parent, stream, params, stats=True)
+                bm_c.append(st["nnz_reached"] / 2.0)
+            reps = 5
+            a.record(stream)
+            for _ in range(reps):
+                plan.launch(stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            bms = a.elapsed_time(b) / reps
+            a.record(stream)
+            for s in bs:
+                abfs.run(G, int(s), level, parent, stream, params)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sms = a.elapsed_time(b)
+            line["batched"] = {"queries": 64, "launch": "one persistent launch, CUDA graph replay",
+                               "ms": bms, "gteps": sum(bm_c) / (bms * 1e-3) / 1e9,
+                               "single_query_ms": sms,
+                               "single_query_gteps": sum(bm_c) / (sms * 1e-3) / 1e9,
+                               "speedup_vs_single": sms / bms}
+            plan.destroy()
+
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, srcs)
+    G.destroy()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -75,10 +75,10 @@ typedef enum {
  * abfs_tune() measures and picks them for a graph. */
 typedef struct {
     uint32_t mode;            /* ABFS_MODE_SUBMATRIX or ABFS_MODE_PLAIN */
-    uint32_t tile;            /* frontier vertices per work unit, 32..2048, multiple of 32 */
-    uint32_t heavy_degree;    /* columns with >= this many entries are split into chunks */
-    uint32_t chunk;           /* entries per heavy-column chunk, multiple of 128 */
-    uint32_t narrow_max;      /* frontiers of <= this many vertices run on one CTA; <= tile */
+    uint32_t tile;            /* frontier vertices staged per step, 32..1024, multiple of 32 */
+    uint32_t unit_entries;    /* entry slots per work unit, 256..16384, multiple of 256 */
+    uint32_t narrow_max;      /* frontiers of <= this many vertices ... */
+    uint32_t narrow_edges;    /* ... and <= this many column entries run on one CTA */
     uint32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x SM count (capped by occupancy) */
     float shrink_theta;       /* physical shrink once the reached fraction of n crosses theta;
                                  <= 0 or >= 1 disables it */
@@ -121,7 +121,7 @@ int abfs_default_params(abfs_params* p);
  * (for device input, after a copy back).  `directed` does not change the
  * traversal; it selects validation and the edge convention of reports.
  * Synchronises `stream` before returning.
- * Limits: n < 2^31, nnz < 2^32.
+ * Limits: n < 2^31, nnz + n < 2^32.
  */
 int abfs_graph_create(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, uint64_t nnz,
                       int directed, uint32_t flags, abfs_stream_t stream, abfs_graph_t* out);
@@ -155,6 +155,20 @@ int abfs_run(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,
  */
 int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_host, int32_t* parent_host,
                   abfs_stream_t stream, const abfs_params* params, abfs_stats* stats);
+
+/*
+ * abfs_run plus a per-phase trace of the search, for profiling: trace_host
+ * receives up to `cap` entries of 8 uint32 each --
+ *   [0..1] %globaltimer (ns, low/high), [2] phase kind << 24 | BFS level
+ *   (kind 0 level, 1 comparator multiply, 2 comparator mask, 3 shrink,
+ *   0xFE start, 0xFF end), [3] 1 if the phase ran on one CTA,
+ *   [4] heavy-chunk units, [5] frontier vertices (or touched rows),
+ *   [6] column entries of that frontier, [7] 0.
+ * *count receives the number written.  Synchronises `stream`.
+ */
+int abfs_run_trace(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,
+                   abfs_stream_t stream, const abfs_params* params, uint32_t* trace_host,
+                   uint32_t cap, uint32_t* count);
 
 /*
  * Batched search: `count` independent searches (graph g[i], source

@@ -20,6 +20,7 @@ from .binding import (  # noqa: F401
     run,
     run_batch,
     run_host,
+    run_trace,
     strerror,
     tune,
 )

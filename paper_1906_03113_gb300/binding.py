@@ -38,9 +38,9 @@ class Params(ctypes.Structure):
     _fields_ = [
         ("mode", ctypes.c_uint32),
         ("tile", ctypes.c_uint32),
-        ("heavy_degree", ctypes.c_uint32),
-        ("chunk", ctypes.c_uint32),
+        ("unit_entries", ctypes.c_uint32),
         ("narrow_max", ctypes.c_uint32),
+        ("narrow_edges", ctypes.c_uint32),
         ("ctas_per_sm", ctypes.c_uint32),
         ("shrink_theta", ctypes.c_float),
         ("shrink_max", ctypes.c_uint32),
@@ -113,6 +113,7 @@ def load():
         "abfs_graph_footprint": ([vp, P(Params), P(ctypes.c_size_t)], c_int),
         "abfs_run": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
         "abfs_run_host": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
+        "abfs_run_trace": ([vp, u32, vp, vp, vp, P(Params), vp, u32, P(u32)], c_int),
         "abfs_run_batch": ([P(vp), P(u32), u32, P(vp), P(vp), vp, P(Params), P(i32)], c_int),
         "abfs_batch_create": ([P(vp), P(u32), u32, P(vp), P(vp), P(Params), vp, P(vp)], c_int),
         "abfs_batch_launch": ([vp, vp], c_int),
@@ -243,6 +244,43 @@ def run(g: Graph, source: int, level=None, parent=None, stream=None, params: Par
                          ctypes.byref(st) if st else None)
     _check(rc, "abfs_run")
     return (level, parent, st.as_dict()) if stats else (level, parent)
+
+
+TRACE_KINDS = {0: "level", 1: "plain_mult", 2: "plain_mask", 3: "shrink", 0xFE: "start",
+               0xFF: "end"}
+
+
+def run_trace(g: Graph, source: int, params: Params | None = None, cap: int = 4096, stream=None):
+    """abfs_run_trace: (level, parent, list of per-phase dicts with t_us from start)."""
+    import torch
+    level, parent = _outputs(g.n, None, None, torch.device("cuda", torch.cuda.current_device()))
+    buf = np.zeros(cap * 8, dtype=np.uint32)
+    cnt = ctypes.c_uint32()
+    rc = load().abfs_run_trace(g.handle, int(source), level.data_ptr(), parent.data_ptr(),
+                               _stream_ptr(stream), ctypes.byref(params) if params else None,
+                               buf.ctypes.data, cap, ctypes.byref(cnt))
+    _check(rc, "abfs_run_trace")
+    rows = buf[: cnt.value * 8].reshape(-1, 8).astype(np.uint64)
+    out = []
+    t0 = None
+    prof_at = [i for i, r in enumerate(rows) if (int(r[2]) >> 24) == 0xFD]
+    if prof_at:
+        flat = rows[prof_at[0]:prof_at[0] + 3].reshape(-1)[4:]
+        vals = [int(flat[2 * q] | (flat[2 * q + 1] << 32)) for q in range(8)]
+        names = ["idle", "take", "gather", "expand", "wait", "flush", "advance", "units"]
+        out_prof = dict(zip(names, vals))
+        rows = rows[:prof_at[0]]
+    else:
+        out_prof = {}
+    for r in rows:
+        t = int(r[0] | (r[1] << 32))
+        t0 = t if t0 is None else t0
+        out.append({"t_us": (t - t0) / 1e3, "kind": TRACE_KINDS.get(int(r[2]) >> 24, int(r[2]) >> 24),
+                    "level": int(r[2]) & 0xFFFFFF, "alone": int(r[3]), "items": int(r[4]),
+                    "vertices": int(r[5]), "entries": int(r[6])})
+    if out_prof:
+        out.append({"kind": "profile", **out_prof})
+    return level, parent, out
 
 
 def run_host(g: Graph, source: int, level_host: np.ndarray | None = None,

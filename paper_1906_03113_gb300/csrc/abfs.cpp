@@ -112,9 +112,9 @@ abfs_params default_params() {
     abfs_params p;
     p.mode = ABFS_MODE_SUBMATRIX;
     p.tile = 1024;
-    p.heavy_degree = 4096;
-    p.chunk = 4096;
+    p.unit_entries = 16384;
     p.narrow_max = 1024;
+    p.narrow_edges = 16384;
     p.ctas_per_sm = 2;
     p.shrink_theta = 0.f;
     p.shrink_max = 0;
@@ -130,9 +130,8 @@ bool shrink_enabled(const abfs_params& p) {
 int check_params(const abfs_params& p) {
     if (p.mode > ABFS_MODE_PLAIN) return ABFS_ERR_INVALID_ARG;
     if (p.tile < 32 || p.tile > (uint32_t)kTileMax || p.tile % 32) return ABFS_ERR_INVALID_ARG;
-    if (p.chunk < 128 || p.chunk % 128 || p.chunk > (1u << 24)) return ABFS_ERR_INVALID_ARG;
-    if (p.heavy_degree < p.chunk) return ABFS_ERR_INVALID_ARG;
-    if (p.narrow_max > p.tile) return ABFS_ERR_INVALID_ARG;
+    if (p.unit_entries < 256 || p.unit_entries % 256 || p.unit_entries > kUnitMax)
+        return ABFS_ERR_INVALID_ARG;
     if (p.ctas_per_sm < 1 || p.ctas_per_sm > 8) return ABFS_ERR_INVALID_ARG;
     if (!(p.shrink_theta >= 0.f) || p.shrink_theta > 1.f) return ABFS_ERR_INVALID_ARG;
     if (p.timeout_ms < 1 || p.timeout_ms > 600000) return ABFS_ERR_INVALID_ARG;
@@ -143,9 +142,9 @@ EngineParams engine_params(const abfs_params& p) {
     EngineParams e;
     e.mode = p.mode;
     e.tile = p.tile;
-    e.heavy = p.heavy_degree;
-    e.chunk = p.chunk;
+    e.unit = p.unit_entries;
     e.narrow_max = p.narrow_max;
+    e.narrow_edges = p.narrow_edges;
     e.shrink_theta = shrink_enabled(p) ? p.shrink_theta : 0.f;
     e.shrink_max = shrink_enabled(p) ? std::min<uint32_t>(p.shrink_max, 64) : 0;
     e.shrink_tile = kTileMax;
@@ -154,8 +153,7 @@ EngineParams engine_params(const abfs_params& p) {
 }
 
 bool same_layout(const abfs_params& a, const abfs_params& b) {
-    return a.mode == b.mode && a.chunk == b.chunk && a.heavy_degree == b.heavy_degree &&
-           shrink_enabled(a) == shrink_enabled(b) &&
+    return a.mode == b.mode && a.unit_entries == b.unit_entries && shrink_enabled(a) == shrink_enabled(b) &&
            (!shrink_enabled(a) || std::min(a.shrink_max, 2u) == std::min(b.shrink_max, 2u));
 }
 
@@ -164,10 +162,11 @@ bool same_layout(const abfs_params& a, const abfs_params& b) {
 // ---------------------------------------------------------------------------
 
 struct Layout {
-    size_t bm[2], fq[2], hq[2], y, touched, sbeg[2], slen[2], srows[2], ctl, inst;
+    size_t bm[2], fq[2], fbeg[2], fpre[2], blk[2], ustart[2], y, touched, sbeg[2], slen[2],
+        srows[2], ctl, inst;
     size_t total;
-    uint32_t nwords, hcap, ncopies;
-    unsigned long long scap;
+    uint32_t nwords, bcap, ncopies;
+    unsigned long long ucap, scap;
 };
 
 Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p) {
@@ -181,11 +180,17 @@ Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p) {
         return at;
     };
     L.nwords = (n + 31) / 32;
-    L.hcap = (uint32_t)std::min<uint64_t>(2 * nnz / p.chunk + 64, 0xFFFFFFF0ull);
+    L.bcap = std::min<uint32_t>(n, kBlockMask);
+    L.ucap = (nnz + n) / p.unit_entries + 2;
     L.ctl = take(sizeof(InstCtl));
     L.inst = take(sizeof(Inst));
-    for (int i = 0; i < 2; ++i) L.fq[i] = take((size_t)n * 4);
-    for (int i = 0; i < 2; ++i) L.hq[i] = take((size_t)L.hcap * 8);
+    for (int i = 0; i < 2; ++i) {
+        L.fq[i] = take((size_t)n * 4);
+        L.fbeg[i] = take((size_t)n * 4);
+        L.fpre[i] = take((size_t)n * 4);
+        L.blk[i] = take((size_t)L.bcap * sizeof(Block));
+        L.ustart[i] = take((size_t)L.ucap * sizeof(uint2));
+    }
     if (p.mode == ABFS_MODE_SUBMATRIX)
         for (int i = 0; i < 2; ++i) L.bm[i] = take((size_t)L.nwords * 4);
     if (p.mode == ABFS_MODE_PLAIN) {
@@ -219,8 +224,6 @@ struct Workspace {
     uint32_t* d_done = nullptr;
     unsigned long long* d_beat = nullptr;
     InstCtl* h_ctl = nullptr; // pinned copy for stats
-    int32_t* d_level = nullptr;   // for host-output runs
-    int32_t* d_parent = nullptr;
 };
 
 struct abfs_graph_s {
@@ -235,6 +238,8 @@ struct abfs_graph_s {
     abfs_params tuned_params{};
     std::mutex mu;
     Workspace ws;
+    int32_t* d_level = nullptr;   // device outputs of host-output runs (abfs_run_host)
+    int32_t* d_parent = nullptr;
     cudaEvent_t last_use = nullptr;
     bool used = false;
 };
@@ -267,8 +272,6 @@ void free_workspace(Workspace& w) {
     dev_free(w.base);
     dev_free(w.d_done);
     dev_free(w.d_beat);
-    dev_free(w.d_level);
-    dev_free(w.d_parent);
     if (w.h_ctl) cudaFreeHost(w.h_ctl);
     w = Workspace{};
 }
@@ -282,12 +285,16 @@ Inst make_inst(const abfs_graph_s* g, char* base, const Layout& L, uint32_t src,
     I.n = g->n;
     I.src = src;
     I.nwords = L.nwords;
-    I.hcap = L.hcap;
+    I.bcap = L.bcap;
+    I.ucap = L.ucap;
     I.level = level;
     I.parent = reinterpret_cast<uint32_t*>(parent);
     for (int i = 0; i < 2; ++i) {
         I.fq[i] = reinterpret_cast<uint32_t*>(base + L.fq[i]);
-        I.hq[i] = reinterpret_cast<uint2*>(base + L.hq[i]);
+        I.fbeg[i] = reinterpret_cast<uint32_t*>(base + L.fbeg[i]);
+        I.fpre[i] = reinterpret_cast<uint32_t*>(base + L.fpre[i]);
+        I.blk[i] = reinterpret_cast<Block*>(base + L.blk[i]);
+        I.ustart[i] = reinterpret_cast<uint2*>(base + L.ustart[i]);
         I.bm[i] = L.bm[i] ? reinterpret_cast<uint32_t*>(base + L.bm[i]) : nullptr;
     }
     if (L.y) I.y = reinterpret_cast<unsigned long long*>(base + L.y);
@@ -372,17 +379,20 @@ const abfs_params& pick_params(const abfs_graph_s* g, const abfs_params* params,
 
 // Enqueues one search into g's workspace; caller holds g->mu.
 int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* parent,
-                   cudaStream_t s, const abfs_params& p) {
+                   cudaStream_t s, const abfs_params& p, uint4* trace = nullptr,
+                   uint32_t trace_cap = 0, unsigned long long* prof = nullptr) {
     int rc = ensure_workspace(g, p);
     if (rc) return rc;
     Workspace& w = g->ws;
     if (g->used) CK(cudaStreamWaitEvent(s, g->last_use, 0));
-    CK(launch_set_query(w.d_inst, source, level, reinterpret_cast<uint32_t*>(parent), s));
+    CK(launch_set_query(w.d_inst, source, level, reinterpret_cast<uint32_t*>(parent), trace,
+                        trace_cap, s));
     EngineArgs a;
     a.insts = w.d_inst;
     a.ninst = 1;
     a.done_count = w.d_done;
     a.heartbeat = w.d_beat;
+    a.prof = prof;
     a.p = engine_params(p);
     CK(launch_init(a, g->n, s));
     CK(launch_engine(a, grid_size(g, p, 0), s));
@@ -412,7 +422,7 @@ extern "C" int abfs_graph_create(const uint32_t* colptr, const uint32_t* rowidx,
                                  abfs_graph_t* out) {
     if (!out || !colptr || (nnz && !rowidx) || n == 0) return ABFS_ERR_INVALID_ARG;
     *out = nullptr;
-    if (n >= (1u << 31) || nnz >= (1ull << 32)) return ABFS_ERR_UNSUPPORTED;
+    if (n >= (1u << 31) || nnz + n >= (1ull << 32)) return ABFS_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     const bool on_dev = flags & ABFS_INPUT_ON_DEVICE;
     std::vector<uint32_t> hc, hr;
@@ -457,6 +467,8 @@ extern "C" int abfs_graph_destroy(abfs_graph_t g) {
     if (!g) return ABFS_ERR_INVALID_ARG;
     if (g->used && g->last_use) cudaEventSynchronize(g->last_use);
     free_workspace(g->ws);
+    dev_free(g->d_level);
+    dev_free(g->d_parent);
     dev_free(g->d_colptr);
     dev_free(g->d_rowidx);
     if (g->last_use) cudaEventDestroy(g->last_use);
@@ -507,19 +519,74 @@ extern "C" int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_hos
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g->mu);
-    Workspace& w = g->ws;
-    if (!w.d_level) {
-        rc = dev_alloc((void**)&w.d_level, (size_t)g->n * 4);
-        if (!rc) rc = dev_alloc((void**)&w.d_parent, (size_t)g->n * 4);
+    if (!g->d_level) {
+        rc = dev_alloc((void**)&g->d_level, (size_t)g->n * 4);
+        if (!rc) rc = dev_alloc((void**)&g->d_parent, (size_t)g->n * 4);
         if (rc) return rc;
     }
-    rc = enqueue_single(g, source, w.d_level, w.d_parent, s, p);
+    rc = enqueue_single(g, source, g->d_level, g->d_parent, s, p);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(level_host, w.d_level, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(parent_host, w.d_parent, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(level_host, g->d_level, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(parent_host, g->d_parent, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
     if (stats) return finish_stats(g, s, stats);
     CK(cudaStreamSynchronize(s));
     return ABFS_OK;
+}
+
+extern "C" int abfs_run_trace(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,
+                              abfs_stream_t stream, const abfs_params* params, uint32_t* trace_host,
+                              uint32_t cap, uint32_t* count) {
+    if (!g || !level || !parent || source >= g->n || !trace_host || !count || cap == 0)
+        return ABFS_ERR_INVALID_ARG;
+    abfs_params tmp;
+    const abfs_params& p = pick_params(g, params, tmp);
+    int rc = check_params(p);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint4* d_trace = nullptr;
+    rc = dev_alloc((void**)&d_trace, (size_t)cap * 2 * sizeof(uint4) + kProfSlots * 8);
+    if (rc) return rc;
+    unsigned long long* d_prof =
+        reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(d_trace) + (size_t)cap * 32);
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (cudaMemsetAsync(d_prof, 0, kProfSlots * 8, s) != cudaSuccess) {
+        dev_free(d_trace);
+        return ABFS_ERR_CUDA;
+    }
+    // the last three entries carry the CTA cycle accounting (kind 0xFD):
+    // a header of 4 words, then kProfSlots 64-bit totals
+    const uint32_t tcap = cap > 3 ? cap - 3 : 0;
+    rc = enqueue_single(g, source, level, parent, s, p, d_trace, tcap, d_prof);
+    if (!rc) {
+        abfs_stats st;
+        rc = finish_stats(g, s, &st);
+        const uint32_t n = std::min(g->ws.h_ctl->trace_n, tcap);
+        if (cudaMemcpy(trace_host, d_trace, (size_t)n * 2 * sizeof(uint4), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            rc = ABFS_ERR_CUDA;
+        unsigned long long prof[kProfSlots];
+        if (cudaMemcpy(prof, d_prof, sizeof(prof), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = ABFS_ERR_CUDA;
+        uint32_t* out = trace_host + (size_t)n * 8;
+        if (cap <= 3) out = nullptr;
+        if (out) {
+        out[0] = 0;
+        out[1] = 0;
+        out[2] = 0xFDu << 24;
+        out[3] = 0;
+        for (int q = 0; q < kProfSlots; ++q) {
+            out[4 + 2 * q] = (uint32_t)prof[q];
+            out[5 + 2 * q] = (uint32_t)(prof[q] >> 32);
+        }
+        for (int q = 4 + 2 * kProfSlots; q < 24; ++q) out[q] = 0;
+        }
+        *count = (cap > 3) ? n + 3 : n;
+        // the workspace descriptor keeps no pointer to the freed trace buffer
+        launch_set_query(g->ws.d_inst, 0, nullptr, nullptr, nullptr, 0, s);
+        cudaStreamSynchronize(s);
+    }
+    dev_free(d_trace);
+    return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -618,6 +685,7 @@ extern "C" int abfs_batch_create(const abfs_graph_t* g, const uint32_t* sources,
     a.ninst = count;
     a.done_count = b->d_done;
     a.heartbeat = b->d_beat;
+    a.prof = nullptr;
     a.p = engine_params(p);
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -699,8 +767,9 @@ std::string gpu_name(int dev) {
 
 std::string params_json(const abfs_params& p) {
     std::ostringstream o;
-    o << "\"mode\":" << p.mode << ",\"tile\":" << p.tile << ",\"heavy_degree\":" << p.heavy_degree
-      << ",\"chunk\":" << p.chunk << ",\"narrow_max\":" << p.narrow_max
+    o << "\"mode\":" << p.mode << ",\"tile\":" << p.tile << ",\"unit_entries\":" << p.unit_entries
+      << ",\"narrow_max\":" << p.narrow_max
+      << ",\"narrow_edges\":" << p.narrow_edges
       << ",\"ctas_per_sm\":" << p.ctas_per_sm << ",\"shrink_theta\":" << p.shrink_theta
       << ",\"shrink_max\":" << p.shrink_max;
     return o.str();
@@ -751,9 +820,9 @@ extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count
             abfs_params p = default_params();
             double v;
             if (json_num(found, "tile", &v)) p.tile = (uint32_t)v;
-            if (json_num(found, "heavy_degree", &v)) p.heavy_degree = (uint32_t)v;
-            if (json_num(found, "chunk", &v)) p.chunk = (uint32_t)v;
+            if (json_num(found, "unit_entries", &v)) p.unit_entries = (uint32_t)v;
             if (json_num(found, "narrow_max", &v)) p.narrow_max = (uint32_t)v;
+            if (json_num(found, "narrow_edges", &v)) p.narrow_edges = (uint32_t)v;
             if (json_num(found, "ctas_per_sm", &v)) p.ctas_per_sm = (uint32_t)v;
             if (json_num(found, "shrink_theta", &v)) p.shrink_theta = (float)v;
             if (json_num(found, "shrink_max", &v)) p.shrink_max = (uint32_t)v;
@@ -770,23 +839,20 @@ extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count
     }
     // candidate sets
     std::vector<abfs_params> cands;
-    const uint32_t tiles[] = {512, 1024, 2048};
-    const uint32_t chunks[] = {2048, 8192};
-    const uint32_t narrows[] = {0, 256, 1024};
+    const uint32_t units[] = {4096, 8192, 16384};
+    const uint32_t narrow_e[] = {0, 4096, 32768};
     const uint32_t ctas[] = {1, 2};
-    for (uint32_t t : tiles)
-        for (uint32_t c : chunks)
-            for (uint32_t nm : narrows)
-                for (uint32_t cp : ctas) {
-                    abfs_params p = default_params();
-                    p.mode = mode;
-                    p.tile = t;
-                    p.chunk = c;
-                    p.heavy_degree = c;
-                    p.narrow_max = std::min(nm, t);
-                    p.ctas_per_sm = cp;
-                    cands.push_back(p);
-                }
+    for (uint32_t ue : units)
+        for (uint32_t ne : narrow_e)
+            for (uint32_t cp : ctas) {
+                abfs_params p = default_params();
+                p.mode = mode;
+                p.unit_entries = ue;
+                p.narrow_edges = ne;
+                p.narrow_max = ne ? 2048 : 0;
+                p.ctas_per_sm = cp;
+                cands.push_back(p);
+            }
     if (mode == ABFS_MODE_SUBMATRIX) {
         const float thetas[] = {0.5f, 0.8f, 0.95f};
         for (float th : thetas) {

@@ -1,12 +1,17 @@
 // Persistent BFS engine for sm_103a.
 //
 // One launch runs one or many searches to completion.  Every search advances
-// level by level (Algorithm 1, Section 8): the frontier x_k is split into work
-// units (tiles of frontier vertices, and fixed-size chunks of heavy columns);
-// any CTA may take any unit of any search; the CTA that completes the last unit
-// of a level advances that search to the next level and publishes the next
-// level's units.  Small levels run on the advancing CTA alone ("narrow"
-// levels), so long, thin searches do not pay a grid-wide hand-off per level.
+// level by level (Algorithm 1, Section 8).  The frontier x_k is kept as a list
+// of vertices in blocks; every vertex carries a weight (its column length, at
+// least 1), and the level's column entries form one "entry space" of
+// sum(weights) slots.  Work units are fixed-size ranges of that space, so a
+// unit holds the same number of entries whether it covers one hub column or
+// thousands of short ones (the PRAM "one processor per nonzero" of Theorem 4,
+// with load balance instead of a processor per entry).  Any CTA may take any
+// unit of any search; the CTA that completes the last unit of a level advances
+// the search and publishes the next level.  Small levels run on the advancing
+// CTA alone ("narrow" levels), so long, thin searches do not pay a grid-wide
+// hand-off per level.
 //
 // Submatrix mode (the paper's method, Theorem 1): for frontier column j and
 // row i in column j, the row is first tested against the visited mask V_{k+1};
@@ -21,6 +26,13 @@
 // bitmap collects the level-k frontier and the level-(k+1) claims and becomes
 // the test bitmap of level k+1.
 //
+// Newly reached vertices gather in a CTA staging buffer and leave it as one
+// block (Section 10's per-thread counts and prefix offsets, at CTA scope): a
+// single 64-bit atomicAdd reserves the block's number and its entry range at
+// once, so blocks are ordered by entry range; each vertex records the unit
+// boundaries that fall inside its own range, so every unit of the next level
+// finds its first vertex with one load.
+//
 // Comparator mode (masked SpMSpV, Section 5/Section 11): the multiply runs over
 // every entry of the frontier columns into a stamped (min, index) accumulator,
 // and the visited mask is applied to the touched rows afterwards.
@@ -29,9 +41,10 @@
 // graph crosses a threshold, every still-unvisited column is stream-compacted
 // to its unvisited rows; later levels read the compacted copy.
 //
-// Waits: a CTA without work polls a search's published phase; every poll loop
-// is bounded by a time limit measured on %globaltimer and reset by progress.
-// On expiry the CTA marks the searches failed (ABFS_ERR_TIMEOUT) and returns.
+// Waits: a CTA without work polls the searches' published phases; every poll
+// loop is bounded by a time limit measured on %globaltimer and reset by
+// progress.  On expiry the CTA marks the searches failed (ABFS_ERR_TIMEOUT) and
+// returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -53,13 +66,11 @@ __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long l
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
@@ -69,8 +80,13 @@ __device__ __forceinline__ uint64_t globaltimer() {
 // Read of data written earlier in this launch by other CTAs (L2, not L1).
 __device__ __forceinline__ uint32_t ld_l2(const uint32_t* p) { return __ldcg(p); }
 __device__ __forceinline__ uint2 ld_l2(const uint2* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ld_l2(const unsigned long long* p) { return __ldcg(p); }
 // Read of data that no CTA writes during the launch.
 __device__ __forceinline__ uint32_t ld_ro(const uint32_t* p) { return __ldg(p); }
+// Read of data that no CTA writes during the current phase (the frozen test
+// bitmap): a plain load that may hit L1.  Every unit starts after an acquire
+// fence, which orders it after the writes of earlier phases.
+__device__ __forceinline__ uint32_t ld_frozen(const uint32_t* p) { return *p; }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -89,29 +105,55 @@ struct Cmd {
     uint32_t unit;
     uint32_t kind;
     uint32_t level;
-    uint32_t nheavy;
     uint32_t nitems;
     uint32_t last;     // this CTA completed the last unit of the phase
     uint32_t quit;
 };
 
 struct Smem {
+    // staged frontier vertices of the unit being expanded: id, column begin
+    // minus slot offset (row index of slot s is b[t] + s), slot offset, and
+    // end of the vertex's entry slots
     uint32_t v[kTileMax + 1];
-    uint32_t b[kTileMax];
+    uint32_t b[kTileMax + 1];
     uint32_t off[kTileMax + 1];
-    uint32_t out[kOutBuf];
-    uint32_t out_cnt;
-    uint32_t out_valid;
+    uint32_t end[kTileMax];
+    // bit (s - lo) set when slot s starts a staged vertex
+    uint32_t sbits[kStartWords];
+    // newly reached vertices staged per warp before a global append
+    uint32_t wv[kWarps][kWarpBuf];
+    uint32_t wcnt[kWarps];
+    uint32_t wvoff[kWarps + 1];
+    uint32_t wwoff[kWarps + 1];
     uint32_t gbase;
+    uint32_t gblk;
+    unsigned long long geb;
     uint32_t warp_sums[kWarps + 1];
+    // walk state of the current unit
+    uint32_t cur_b, cur_i, abort_unit, sub_cnt, sub_nseg;
+    unsigned long long sub_g0, sub_end;
+    uint32_t seg_idx[32], seg_pos[32];
+    unsigned long long seg_eb[32];
     unsigned long long st_read, st_unmasked, st_claims, st_nnz;
     Cmd cmd;
     Inst I;
     uint32_t cur_q;
+    uint32_t prof_on;
+    unsigned long long prof[kProfSlots];
 };
 
+// Profiling runs: thread 0 adds the cycles since t0 to slot `slot`.
+__device__ __forceinline__ long long prof_now(const Smem& sm) {
+    return sm.prof_on ? clock64() : 0ll;
+}
+__device__ __forceinline__ void prof_add(Smem& sm, int slot, long long t0) {
+    if (sm.prof_on && threadIdx.x == 0) sm.prof[slot] += (unsigned long long)(clock64() - t0);
+}
+
+size_t engine_smem_bytes() { return sizeof(Smem); }
+
 // ---------------------------------------------------------------------------
-// small block-level building blocks
+// block-level building blocks
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
@@ -124,15 +166,15 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
     return x;
 }
 
-// Exclusive scan of a[0..cnt) in place; a[cnt] = total.  cnt <= kThreads*4.
+// Exclusive scan of a[0..cnt) in place; a[cnt] = total.  cnt <= kThreads*ITEMS.
+template <int ITEMS>
 __device__ void block_exclusive_scan(uint32_t* a, uint32_t cnt, Smem& sm) {
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kItems = kTileMax / kThreads;
-    uint32_t x[kItems];
+    uint32_t x[ITEMS];
     uint32_t sum = 0;
 #pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-        uint32_t idx = tid * kItems + q;
+    for (int q = 0; q < ITEMS; ++q) {
+        uint32_t idx = tid * ITEMS + q;
         x[q] = idx < cnt ? a[idx] : 0u;
         sum += x[q];
     }
@@ -148,126 +190,227 @@ __device__ void block_exclusive_scan(uint32_t* a, uint32_t cnt, Smem& sm) {
     __syncthreads();
     uint32_t run = sm.warp_sums[warp] + incl - sum;
 #pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-        uint32_t idx = tid * kItems + q;
+    for (int q = 0; q < ITEMS; ++q) {
+        uint32_t idx = tid * ITEMS + q;
         if (idx < cnt) a[idx] = run;
         run += x[q];
     }
     if (tid == 0) a[cnt] = sm.warp_sums[kWarps];
     __syncthreads();
 }
+constexpr int kTileItems = kTileMax / kThreads;
 
-// Column location of vertex v for a search at BFS level `lvl`: which matrix
-// (input or a shrunk copy) holds its current column.
+// Column of vertex v in matrix `mat` (0 = input, 1/2 = shrunk copies).
 struct ColRef {
     uint32_t beg;
     uint32_t len;
-    const uint32_t* rows;
 };
 
 __device__ __forceinline__ ColRef col_of(const Inst& I, uint32_t mat, uint32_t v) {
     ColRef c;
     if (mat == 0) {
-        uint32_t b = ld_ro(I.colptr + v);
-        uint32_t e = ld_ro(I.colptr + v + 1);
+        const uint32_t b = ld_ro(I.colptr + v);
+        const uint32_t e = ld_ro(I.colptr + v + 1);
         c.beg = b;
         c.len = e - b;
-        c.rows = I.rowidx;
     } else {
-        const uint32_t s = mat - 1;
-        c.beg = ld_l2(I.sbeg[s] + v);
-        c.len = ld_l2(I.slen[s] + v);
-        c.rows = I.srows[s];
+        c.beg = ld_l2(I.sbeg[mat - 1] + v);
+        c.len = ld_l2(I.slen[mat - 1] + v);
     }
     return c;
 }
 
+__device__ __forceinline__ const uint32_t* rows_of(const Inst& I, uint32_t mat) {
+    return mat == 0 ? I.rowidx : I.srows[mat - 1];
+}
+
 __device__ __forceinline__ uint32_t mat_for_level(const InstCtl* ctl, uint32_t lvl) {
-    // mat_cur/mat_prev/mat_switch change only at a level boundary, between
-    // phases; the acquire at the start of a unit orders these reads.
-    uint32_t sw = ld_relaxed(&ctl->mat_switch);
+    // mat_cur/mat_prev/mat_switch change only between phases; the acquire at
+    // the start of a unit orders these reads.
+    const uint32_t sw = ld_relaxed(&ctl->mat_switch);
     return lvl >= sw ? ld_relaxed(&ctl->mat_cur) : ld_relaxed(&ctl->mat_prev);
 }
 
-__device__ __forceinline__ void fail(InstCtl* ctl, uint32_t code) {
-    atomicCAS(&ctl->err, 0u, code);
+__device__ __forceinline__ void fail(InstCtl* ctl, uint32_t code) { atomicCAS(&ctl->err, 0u, code); }
+
+// L2 policy for the streamed row indices: evict first, so the search's hot
+// state (bitmaps, parents, column pointers, queues) stays resident.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// Row index load: the input matrix never changes during a launch (read-only
+// path); shrunk copies are written by earlier phases of the same launch.
+__device__ __forceinline__ uint32_t ld_row(const uint32_t* rows, uint32_t idx, uint32_t mat,
+                                           uint64_t pol) {
+    uint32_t v;
+    if (mat == 0)
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;"
+            : "=r"(v)
+            : "l"(rows + idx), "l"(pol));
+    else
+        asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;"
+                     : "=r"(v)
+                     : "l"(rows + idx), "l"(pol)
+                     : "memory");
+    return v;
 }
 
 // ---------------------------------------------------------------------------
-// appending newly reached vertices
+// appending newly reached vertices as frontier blocks
 // ---------------------------------------------------------------------------
 
-// Warp-aggregated append of `val` (where `want`) into the CTA staging buffer;
-// overflow goes straight to the global queue.  All 32 lanes must call.
-__device__ __forceinline__ void append_warp(bool want, uint32_t val, Smem& sm, uint32_t* gq,
-                                            uint32_t* gcnt, uint32_t gcap, InstCtl* ctl) {
-    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, want);
-    if (!mask) return;
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t leader = __ffs(mask) - 1;
-    const uint32_t cnt = __popc(mask);
-    const uint32_t rank = __popc(mask & lanemask_lt());
-    uint32_t pos = 0;
-    if (lane == leader) pos = atomicAdd(&sm.out_cnt, cnt);
-    pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-    if (pos + cnt <= (uint32_t)kOutBuf) {
-        if (want) sm.out[pos + rank] = val;
-    } else {
-        uint32_t g = 0;
-        if (lane == leader) {
-            atomicMin(&sm.out_valid, pos);
-            g = atomicAdd(gcnt, cnt);
-        }
-        g = __shfl_sync(0xFFFFFFFFu, g, leader);
-        if (want) {
-            if (g + rank < gcap) gq[g + rank] = val;
-            else fail(ctl, 7 /* ABFS_ERR_DEVICE */);
-        }
+// Vertex i of block blk (entry range [g0, g0 + w)) owns the unit starts that
+// fall inside its range.
+__device__ __forceinline__ void write_unit_starts(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                                  uint32_t pn, uint32_t blk, uint32_t i,
+                                                  unsigned long long g0, uint32_t w) {
+    const unsigned long long U = P.unit;
+    for (unsigned long long x = (g0 + U - 1) / U * U; x < g0 + w; x += U) {
+        const unsigned long long u = x / U;
+        if (u < I.ucap) I.ustart[pn][u] = make_uint2(blk, i);
+        else fail(ctl, 7 /* ABFS_ERR_DEVICE */);
     }
 }
 
-// Block-wide flush of the staging buffer to the global queue.
-__device__ void flush_out(Smem& sm, uint32_t* gq, uint32_t* gcnt, uint32_t gcap, InstCtl* ctl) {
-    __syncthreads();
-    const uint32_t n = min(sm.out_cnt, sm.out_valid);
-    if (threadIdx.x == 0) {
-        uint32_t base = n ? atomicAdd(gcnt, n) : 0u;
-        if (base + n > gcap) {
-            fail(ctl, 7);
-            base = kUnset;
-        }
-        sm.gbase = base;
-    }
-    __syncthreads();
-    const uint32_t base = sm.gbase;
-    if (base != kUnset)
-        for (uint32_t i = threadIdx.x; i < n; i += kThreads) gq[base + i] = sm.out[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        sm.out_cnt = 0;
-        sm.out_valid = kOutBuf;
-    }
-    __syncthreads();
-}
-
-// A vertex r has just joined the frontier of level lvl+1.  Heavy columns go to
-// the heavy-chunk queue here (one thread writes its chunk descriptors); the
-// return value says whether r belongs in the light frontier.
-__device__ __forceinline__ bool route_new(const Inst& I, InstCtl* ctl, const EngineParams& P,
-                                          uint32_t r, uint32_t lvl_next) {
-    const uint32_t mat = mat_for_level(ctl, lvl_next);
-    const ColRef c = col_of(I, mat, r);
-    if (c.len < P.heavy) return true;
-    const uint32_t pn = lvl_next & 1;
-    const uint32_t nch = (c.len + P.chunk - 1) / P.chunk;
-    const uint32_t base = atomicAdd(&ctl->hcnt[pn], nch);
-    atomicAdd(&ctl->hvert[pn], 1u);
-    if (base + nch > I.hcap) {
+// Reserves a block of `cnt` vertices with `wsum` entries in the frontier of
+// parity pn: returns (block number, entry base, vertex base) or fails.
+__device__ __forceinline__ bool reserve_block(const Inst& I, InstCtl* ctl, uint32_t pn, uint32_t cnt,
+                                              uint32_t wsum, uint32_t& blk,
+                                              unsigned long long& eb, uint32_t& vb) {
+    const unsigned long long old =
+        atomicAdd(&ctl->bctr[pn], ((unsigned long long)wsum << kBlockBits) | 1ull);
+    blk = (uint32_t)(old & kBlockMask);
+    eb = old >> kBlockBits;
+    vb = atomicAdd(&ctl->fcnt[pn], cnt);
+    if (blk >= I.bcap || blk >= kBlockMask || (unsigned long long)vb + cnt > I.n) {
         fail(ctl, 7);
         return false;
     }
-    for (uint32_t q = 0; q < nch; ++q) I.hq[pn][base + q] = make_uint2(r, q);
-    return false;
+    Block* B = I.blk[pn] + blk;
+    B->vb = vb;
+    B->nv = cnt;
+    B->eb = eb;
+    return true;
+}
+
+// Warp-aggregated append of newly reached vertex v (where `want`) to this
+// warp's staging buffer; wc is the warp's (uniform) staged count.
+__device__ __forceinline__ void stage_warp(bool want, uint32_t v, Smem& sm, uint32_t& wc) {
+    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, want);
+    if (!mask) return;
+    if (want) sm.wv[threadIdx.x >> 5][wc + __popc(mask & lanemask_lt())] = v;
+    wc += __popc(mask);
+}
+
+// Total weight (column length + kVertexSlots, matrix mat_next) of this warp's
+// n staged vertices.  Whole warp; the columns are looked up again when the
+// vertices are written, so the staging buffer holds vertex ids only.
+__device__ __forceinline__ uint32_t warp_weight(Smem& sm, const Inst& I, uint32_t mat_next,
+                                                uint32_t n) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t* wv = sm.wv[threadIdx.x >> 5];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int it = 0; it < kWarpBuf / 32; ++it) {
+        const uint32_t i = it * 32 + lane;
+        if (i < n) sum += col_of(I, mat_next, wv[i]).len + kVertexSlots;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, d);
+    return sum;
+}
+
+// Writes this warp's n staged vertices at fq[vb + voff ..] of block blk (entry
+// base eb), the group starting at weight offset woff within the block.
+// Whole warp.
+__device__ __forceinline__ void warp_emit(Smem& sm, const Inst& I, InstCtl* ctl,
+                                          const EngineParams& P, uint32_t pn, uint32_t mat_next,
+                                          uint32_t n, uint32_t blk, unsigned long long eb,
+                                          uint32_t vb, uint32_t voff, uint32_t woff) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t* wv = sm.wv[threadIdx.x >> 5];
+    uint32_t carry = woff;
+    for (uint32_t base = 0; base < n; base += 32) {
+        const uint32_t i = base + lane;
+        ColRef c;
+        c.beg = 0;
+        c.len = 0;
+        uint32_t v = 0;
+        if (i < n) {
+            v = wv[i];
+            c = col_of(I, mat_next, v);
+        }
+        const uint32_t w = i < n ? c.len + kVertexSlots : 0u;
+        const uint32_t incl = warp_incl_scan(w);
+        if (i < n) {
+            const uint32_t at = vb + voff + i;
+            const uint32_t pre = carry + incl - w;
+            I.fq[pn][at] = v;
+            I.fbeg[pn][at] = c.beg;
+            I.fpre[pn][at] = pre;
+            write_unit_starts(I, ctl, P, pn, blk, voff + i, eb + pre, w);
+        }
+        carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+    __syncwarp();
+}
+
+// A warp writes its staging buffer out as a frontier block of its own.
+__device__ void warp_flush(Smem& sm, const Inst& I, InstCtl* ctl, const EngineParams& P,
+                           uint32_t pn, uint32_t mat_next, uint32_t& wc) {
+    const uint32_t n = wc;
+    const uint32_t wtot = warp_weight(sm, I, mat_next, n);
+    uint32_t blk = 0, vb = 0, ok = 0;
+    unsigned long long eb = 0;
+    if ((threadIdx.x & 31) == 0) ok = reserve_block(I, ctl, pn, n, wtot, blk, eb, vb);
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    blk = __shfl_sync(0xFFFFFFFFu, blk, 0);
+    vb = __shfl_sync(0xFFFFFFFFu, vb, 0);
+    eb = __shfl_sync(0xFFFFFFFFu, eb, 0);
+    if (ok) warp_emit(sm, I, ctl, P, pn, mat_next, n, blk, eb, vb, 0u, 0u);
+    wc = 0;
+}
+
+// End of a unit: the leftovers of all warps (counts in sm.wcnt) leave as one
+// frontier block.  Whole CTA.
+__device__ void cta_flush(Smem& sm, const Inst& I, InstCtl* ctl, const EngineParams& P,
+                          uint32_t pn, uint32_t mat_next) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    const uint32_t n = sm.wcnt[warp];
+    const uint32_t wtot = warp_weight(sm, I, mat_next, n);
+    if (lane == 0) {
+        sm.wvoff[warp] = n;
+        sm.wwoff[warp] = wtot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t v = 0, w = 0;
+        for (int q = 0; q < kWarps; ++q) {
+            const uint32_t a = sm.wvoff[q], b = sm.wwoff[q];
+            sm.wvoff[q] = v;
+            sm.wwoff[q] = w;
+            v += a;
+            w += b;
+        }
+        sm.wvoff[kWarps] = v;
+        sm.wwoff[kWarps] = w;
+        uint32_t blk = 0, vb = 0;
+        unsigned long long eb = 0;
+        const bool ok = v ? reserve_block(I, ctl, pn, v, w, blk, eb, vb) : false;
+        sm.gblk = ok ? blk : kUnset;
+        sm.geb = eb;
+        sm.gbase = vb;
+    }
+    __syncthreads();
+    if (sm.gblk != kUnset && n)
+        warp_emit(sm, I, ctl, P, pn, mat_next, n, sm.gblk, sm.geb, sm.gbase, sm.wvoff[warp],
+                  sm.wwoff[warp]);
+    if (lane == 0) sm.wcnt[warp] = 0;
+    __syncthreads();
 }
 
 // Comparator accumulator key of frontier column j at level k: the high word is
@@ -278,40 +421,99 @@ __device__ __forceinline__ unsigned long long plain_key(uint32_t k, uint32_t j) 
     return ((unsigned long long)plain_stamp(k) << 32) | (unsigned long long)j;
 }
 
-// Row index load: the input matrix never changes during a launch (read-only
-// path); shrunk copies are written by earlier phases of the same launch.
-__device__ __forceinline__ uint32_t ld_row(const uint32_t* rows, uint32_t idx, uint32_t mat) {
-    return mat == 0 ? ld_ro(rows + idx) : ld_l2(rows + idx);
+// Per-thread counters of one work unit.
+struct Tally {
+    uint32_t read = 0;
+    uint32_t unmasked = 0;
+    uint32_t claims = 0;
+};
+
+// ---------------------------------------------------------------------------
+// the per-entry step: mask, multiply, claim -- kIlp entries per thread at once
+// ---------------------------------------------------------------------------
+
+// Entries (r[u] in column j[u]) where act[u], at level k.  Each stage issues
+// kIlp independent memory operations before consuming any.  Submatrix mode
+// appends the vertices of level k+1 to the next frontier; comparator mode
+// appends first-touched rows to the touched list.  All 32 lanes must call.
+template <int MODE>
+__device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                              Smem& sm, uint32_t k, const uint32_t (&r)[kIlp],
+                                              const uint32_t (&j)[kIlp], const bool (&act)[kIlp],
+                                              Tally& t, uint32_t& wc) {
+    const uint32_t p = k & 1;
+    if (MODE == kModeSub) {
+        const uint32_t* test_bm = I.bm[p];
+        uint32_t* write_bm = I.bm[p ^ 1];
+        uint32_t w[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) w[u] = act[u] ? ld_frozen(test_bm + (r[u] >> 5)) : 0xFFFFFFFFu;
+        // rows outside V_{k+1} are masked before the multiply; the (min, index)
+        // product is an atomicMin of j into parent[r], and moving parent[r]
+        // off "unset" claims r for level k+1
+        bool win[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            win[u] = false;
+            if (!((w[u] >> (r[u] & 31)) & 1u)) {
+                ++t.unmasked;
+                ++t.claims;
+                win[u] = atomicMin(I.parent + r[u], j[u]) == kUnset;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            if (win[u]) {
+                I.level[r[u]] = (int32_t)(k + 1);
+                atomicOr(write_bm + (r[u] >> 5), 1u << (r[u] & 31));
+            }
+            stage_warp(win[u], r[u], sm, wc);
+        }
+    } else {
+        // multiply first: every entry reaches the accumulator
+        unsigned long long old[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            old[u] = 0ull;
+            if (act[u]) {
+                ++t.unmasked;
+                ++t.claims;
+                old[u] = atomicMin(I.y + r[u], plain_key(k, j[u]));
+            }
+        }
+        // first touch of row r at this level: it goes to the touched list
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            const bool first = act[u] && (uint32_t)(old[u] >> 32) != plain_stamp(k);
+            const uint32_t mask = __ballot_sync(0xFFFFFFFFu, first);
+            if (mask) {
+                const uint32_t lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+                uint32_t base = 0;
+                if (lane == leader) base = atomicAdd(&ctl->tcnt, (uint32_t)__popc(mask));
+                base = __shfl_sync(0xFFFFFFFFu, base, leader);
+                if (first) {
+                    const uint32_t at = base + __popc(mask & lanemask_lt());
+                    if (at < I.n) I.touched[at] = r[u];
+                    else fail(ctl, 7);
+                }
+            }
+        }
+    }
 }
 
-// ---------------------------------------------------------------------------
-// the per-entry step: mask, multiply, claim
-// ---------------------------------------------------------------------------
-
-// Submatrix mode: row r of frontier column j at level k.
-__device__ __forceinline__ bool claim_sub(const Inst& I, InstCtl* ctl, const EngineParams& P,
-                                          const uint32_t* test_bm, uint32_t* write_bm, uint32_t r,
-                                          uint32_t j, uint32_t k, uint32_t& unmasked,
-                                          uint32_t& claims, bool& light) {
-    light = false;
-    const uint32_t w = ld_l2(test_bm + (r >> 5));
-    if ((w >> (r & 31)) & 1u) return false;  // row outside V_{k+1}: masked before the multiply
-    ++unmasked;
-    const uint32_t cur = ld_relaxed(I.parent + r);
-    if (cur <= j) return false;  // a smaller parent is already in place; product cannot win
-    ++claims;
-    const uint32_t old = atomicMin(I.parent + r, j);
-    if (old != kUnset) return false;
-    // first product into row r: r joins x_{k+1}
-    I.level[r] = (int32_t)(k + 1);
-    atomicOr(write_bm + (r >> 5), 1u << (r & 31));
-    light = route_new(I, ctl, P, r, k + 1);
-    return true;
+__device__ __forceinline__ void tally_flush(Smem& sm, Tally t) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        t.read += __shfl_xor_sync(0xFFFFFFFFu, t.read, d);
+        t.unmasked += __shfl_xor_sync(0xFFFFFFFFu, t.unmasked, d);
+        t.claims += __shfl_xor_sync(0xFFFFFFFFu, t.claims, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (t.read) atomicAdd(&sm.st_read, (unsigned long long)t.read);
+        if (t.unmasked) atomicAdd(&sm.st_unmasked, (unsigned long long)t.unmasked);
+        if (t.claims) atomicAdd(&sm.st_claims, (unsigned long long)t.claims);
+    }
 }
-
-// ---------------------------------------------------------------------------
-// work units
-// ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void stats_flush(Smem& sm, InstCtl* ctl) {
     __syncthreads();
@@ -324,153 +526,232 @@ __device__ __forceinline__ void stats_flush(Smem& sm, InstCtl* ctl) {
     }
 }
 
-__device__ __forceinline__ void warp_stats(Smem& sm, uint32_t unmasked, uint32_t claims) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        unmasked += __shfl_xor_sync(0xFFFFFFFFu, unmasked, d);
-        claims += __shfl_xor_sync(0xFFFFFFFFu, claims, d);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (unmasked) atomicAdd(&sm.st_unmasked, (unsigned long long)unmasked);
-        if (claims) atomicAdd(&sm.st_claims, (unsigned long long)claims);
-    }
-}
+// ---------------------------------------------------------------------------
+// work units
+// ---------------------------------------------------------------------------
 
-// Expands the entries e in [e0, e1) of the tile described by sm.v/sm.b/sm.off
-// (cnt columns).  Each lane walks its own column cursor forward.
+// Expands the slots [l0, l1) of the staged vertices (cnt of them; sm.off holds
+// their first slots, sm.off[cnt] the end; sm.sbits marks the first slots that
+// fall in [l0, l1)).  Slot s of vertex t is the column entry with row index
+// b[t] + s if s < end[t]; the kVertexSlots slots after its entries are empty.
+// The slots are split evenly over the warps; a warp takes 32 consecutive
+// slots per group (coalesced row loads) and kIlp groups per step.  The vertex
+// of slot s is a prefix count of vertex starts, read from sm.sbits with one
+// popcount.  The row loads of step s+1 are issued before step s is processed.
 template <int MODE>
-__device__ void expand_entries(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                               uint32_t cnt, uint32_t e0, uint32_t e1, const uint32_t* rows,
-                               uint32_t mat, uint32_t k) {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t p = k & 1;
-    const uint32_t* test_bm = I.bm[p];
-    uint32_t* write_bm = I.bm[p ^ 1];
-    uint32_t unmasked = 0, claims = 0;
-    // initial column of this lane: last i with off[i] <= e
-    uint32_t e = e0 + lane;
-    uint32_t i = 0;
-    if (e < e1) {
-        uint32_t lo = 0, hi = cnt;  // off[lo] <= e < off[hi]
+__device__ void expand_slots(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+                             uint32_t cnt, uint32_t l0, uint32_t l1, uint32_t mat, uint32_t k,
+                             Tally& t) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t span = l1 - l0;
+    const uint32_t per = (span + kWarps - 1) / kWarps;
+    const uint32_t e0 = l0 + min(span, warp * per);
+    const uint32_t e1 = l0 + min(span, warp * per + per);
+    const uint32_t* rows = rows_of(I, mat);
+    const uint64_t pol = evict_first_policy();
+    const uint32_t le_mask = (2u << lane) - 1u;  // lanes 0..lane
+    // vertex(s) = vb + (number of vertex starts in [e0, s])
+    uint32_t vb = 0;
+    if (e0 < e1) {
+        uint32_t lo = 0, hi = cnt;  // off[lo] <= e0 < off[hi]
         while (hi - lo > 1) {
-            uint32_t mid = (lo + hi) >> 1;
-            if (sm.off[mid] <= e) lo = mid;
+            const uint32_t mid = (lo + hi) >> 1;
+            if (sm.off[mid] <= e0) lo = mid;
             else hi = mid;
         }
-        i = lo;
+        vb = lo - (sm.off[lo] == e0 ? 1u : 0u);
     }
-    for (uint32_t base = e0; base < e1; base += 32, e += 32) {
-        bool active = e < e1;
-        bool want = false;
-        uint32_t r = 0;
-        if (active) {
-            while (sm.off[i + 1] <= e) ++i;
-            const uint32_t j = sm.v[i];
-            r = ld_row(rows, sm.b[i] + (e - sm.off[i]), mat);
-            if (MODE == kModeSub) {
-                bool light;
-                claim_sub(I, ctl, P, test_bm, write_bm, r, j, k, unmasked, claims, light);
-                want = light;
-            } else {
-                // multiply first: every entry reaches the accumulator
-                ++unmasked;
-                ++claims;
-                const unsigned long long old = atomicMin(I.y + r, plain_key(k, j));
-                want = (uint32_t)(old >> 32) != plain_stamp(k);  // first touch of row r this level
+    uint32_t starts = 0;  // vertex starts in [e0, current group base)
+    uint32_t r[kIlp], j[kIlp];
+    bool act[kIlp];
+    auto load_step = [&](uint32_t base, uint32_t (&rr)[kIlp], uint32_t (&jj)[kIlp],
+                         bool (&aa)[kIlp]) {
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            const uint32_t gb = base + 32 * u;
+            const uint32_t rel = gb - l0;
+            const uint32_t sh = rel & 31;
+            uint32_t w = sm.sbits[rel >> 5] >> sh;
+            if (sh) w |= sm.sbits[(rel >> 5) + 1] << (32 - sh);
+            const uint32_t s = gb + lane;
+            const uint32_t v = vb + starts + __popc(w & le_mask);
+            starts += __popc(w);
+            aa[u] = false;
+            rr[u] = 0;
+            jj[u] = 0;
+            if (s < e1 && s < sm.end[v]) {
+                aa[u] = true;
+                jj[u] = sm.v[v];
+                rr[u] = ld_row(rows, sm.b[v] + s, mat, pol);
             }
         }
-        if (MODE == kModeSub)
-            append_warp(want, r, sm, I.fq[p ^ 1], &ctl->fcnt[p ^ 1], I.n, ctl);
-        else
-            append_warp(want, r, sm, I.touched, &ctl->tcnt, I.n, ctl);
+    };
+    uint32_t wc = sm.wcnt[warp];
+    const uint32_t mat_next = mat_for_level(ctl, k + 1);
+    if (e0 < e1) load_step(e0, r, j, act);
+    for (uint32_t base = e0; base < e1; base += 32 * kIlp) {
+        uint32_t r2[kIlp], j2[kIlp];
+        bool act2[kIlp];
+        if (base + 32 * kIlp < e1) {
+            load_step(base + 32 * kIlp, r2, j2, act2);
+        } else {
+#pragma unroll
+            for (int u = 0; u < kIlp; ++u) {
+                act2[u] = false;
+                r2[u] = j2[u] = 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) t.read += act[u];
+        process_group<MODE>(I, ctl, P, sm, k, r, j, act, t, wc);
+        if (MODE == kModeSub && wc > (uint32_t)kWarpFlushAt)
+            warp_flush(sm, I, ctl, P, (k + 1) & 1, mat_next, wc);
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            r[u] = r2[u];
+            j[u] = j2[u];
+            act[u] = act2[u];
+        }
     }
-    warp_stats(sm, unmasked, claims);
+    if (lane == 0) sm.wcnt[warp] = wc;
+    __syncwarp();
 }
 
-// A tile of light frontier vertices at level k.
+// Unit u of the level-k frontier: entry slots [u*U, min((u+1)*U, total)).
+// The unit walks the frontier blocks in entry order from the vertex recorded
+// in ustart[u], staging up to `tile` vertices from up to 32 blocks at a time.
 template <int MODE>
-__device__ void unit_light(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                           uint32_t k, uint32_t tile_idx, uint32_t nf) {
+__device__ void unit_level(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+                           uint32_t k, uint32_t u) {
     const uint32_t p = k & 1;
-    const uint32_t base = tile_idx * P.tile;
-    const uint32_t cnt = min(P.tile, nf - base);
+    const unsigned long long bc = ld_relaxed64(&ctl->bctr[p]);
+    const unsigned long long total = bc >> kBlockBits;
+    const uint32_t nb = (uint32_t)(bc & kBlockMask);
+    const unsigned long long u_lo = (unsigned long long)u * P.unit;
+    const unsigned long long u_hi = min(total, u_lo + P.unit);
     const uint32_t mat = mat_for_level(ctl, k);
-    const uint32_t* fq = I.fq[p];
-    uint32_t nnz_local = 0;
-    for (uint32_t t = threadIdx.x; t < cnt; t += kThreads) {
-        const uint32_t v = ld_l2(fq + base + t);
-        const ColRef c = col_of(I, mat, v);
-        sm.v[t] = v;
-        sm.b[t] = c.beg;
-        sm.off[t] = c.len;
-        if (MODE == kModeSub) atomicOr(I.bm[p ^ 1] + (v >> 5), 1u << (v & 31));
-        nnz_local += (mat == 0) ? c.len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
+    const Block* blk = I.blk[p];
+    if (threadIdx.x == 0) {
+        const uint2 st = ld_l2(I.ustart[p] + u);
+        sm.cur_b = st.x;
+        sm.cur_i = st.y;
     }
-    // reached-column nonzeros (input matrix), for reports
+    __syncthreads();
+    Tally t;
+    unsigned long long e = u_lo;
+    uint32_t nnz_local = 0;
+    while (e < u_hi) {
+        const long long pt0 = prof_now(sm);
+        // warp 0: the next up-to-32 blocks, as segments of this sub-tile
+        if (threadIdx.x < 32) {
+            const uint32_t lane = threadIdx.x;
+            const uint32_t b = sm.cur_b + lane;
+            uint32_t vb = 0, nv = 0;
+            unsigned long long eb = total;
+            if (b < nb && b < I.bcap) {
+                vb = ld_l2(&blk[b].vb);
+                nv = ld_l2(&blk[b].nv);
+                eb = ld_l2(&blk[b].eb);
+            }
+            const uint32_t i0 = lane == 0 ? sm.cur_i : 0u;
+            const uint32_t avail = (b < nb && nv > i0) ? nv - i0 : 0u;
+            // entry position of the segment's first vertex
+            unsigned long long start = eb;
+            if (lane == 0 && avail) start = eb + ld_l2(I.fpre[p] + vb + i0);
+            const uint32_t incl = warp_incl_scan(avail);
+            const uint32_t excl = incl - avail;
+            uint32_t take = 0;
+            if (avail && start < u_hi && excl < P.tile) take = min(avail, P.tile - excl);
+            const uint32_t tmask = __ballot_sync(0xFFFFFFFFu, take > 0);
+            const uint32_t nseg = __popc(tmask);  // a prefix of the lanes
+            const uint32_t ntake = __shfl_sync(0xFFFFFFFFu, excl + take, nseg ? nseg - 1 : 0);
+            if (take) {
+                sm.seg_idx[lane] = vb + i0;
+                sm.seg_pos[lane] = excl;
+                sm.seg_eb[lane] = eb;
+            }
+            const unsigned long long eb_next = __shfl_down_sync(0xFFFFFFFFu, eb, 1);
+            if (nseg && lane == nseg - 1) {
+                // end slot of the last staged vertex, and where the next sub-tile starts
+                const uint32_t last_i = i0 + take;  // one past the last staged vertex
+                unsigned long long end;
+                if (last_i < nv) {
+                    end = eb + ld_l2(I.fpre[p] + vb + last_i);
+                    sm.cur_b = b;
+                    sm.cur_i = last_i;
+                } else {
+                    end = (b + 1 >= nb) ? total : (lane < 31 ? eb_next : ld_l2(&blk[b + 1].eb));
+                    sm.cur_b = b + 1;
+                    sm.cur_i = 0;
+                }
+                sm.sub_end = end;
+            }
+            if (lane == 0) {
+                sm.sub_cnt = nseg ? ntake : 0u;
+                sm.sub_nseg = nseg;
+                sm.sub_g0 = start;
+                // the first segment must contain slot e: otherwise an invariant broke
+                sm.abort_unit = (!(tmask & 1u) || start > e) ? 1u : 0u;
+            }
+        }
+        __syncthreads();
+        if (sm.abort_unit) {
+            if (threadIdx.x == 0) fail(ctl, 7);
+            break;
+        }
+        const uint32_t cnt = sm.sub_cnt, nseg = sm.sub_nseg;
+        const unsigned long long g0 = sm.sub_g0;
+        for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
+            uint32_t q = 0, hi = nseg;  // seg_pos[q] <= s < seg_pos[hi]
+            while (hi - q > 1) {
+                const uint32_t mid = (q + hi) >> 1;
+                if (sm.seg_pos[mid] <= s) q = mid;
+                else hi = mid;
+            }
+            const uint32_t idx = sm.seg_idx[q] + (s - sm.seg_pos[q]);
+            sm.v[s] = ld_l2(I.fq[p] + idx);
+            sm.b[s] = ld_l2(I.fbeg[p] + idx);
+            sm.off[s] = (uint32_t)(sm.seg_eb[q] + ld_l2(I.fpre[p] + idx) - g0);
+        }
+        if (threadIdx.x == 0) sm.off[cnt] = (uint32_t)(sm.sub_end - g0);
+        // slots [lo, hi) of this sub-tile belong to the unit
+        const uint32_t lo = (uint32_t)(e - g0);
+        const uint32_t hi_s = (uint32_t)(min(u_hi, (unsigned long long)sm.sub_end) - g0);
+        const uint32_t nwords = (hi_s - lo + 31) / 32 + 1;
+        for (uint32_t w = threadIdx.x; w < nwords; w += kThreads) sm.sbits[w] = 0u;
+        __syncthreads();
+        for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
+            const uint32_t st = sm.off[s];
+            const uint32_t len = sm.off[s + 1] - st - kVertexSlots;
+            sm.end[s] = st + len;
+            sm.b[s] -= st;  // row index of slot x is b + x
+            if (st >= lo && st < hi_s) {
+                // the vertex's first slot lies in this unit: it joins the visited
+                // set of the next level's test (once), and starts a run of slots
+                atomicOr(&sm.sbits[(st - lo) >> 5], 1u << ((st - lo) & 31));
+                const uint32_t v = sm.v[s];
+                if (MODE == kModeSub) atomicOr(I.bm[p ^ 1] + (v >> 5), 1u << (v & 31));
+                nnz_local += (mat == 0) ? len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
+            }
+        }
+        __syncthreads();
+        const unsigned long long s_hi = min(u_hi, (unsigned long long)sm.sub_end);
+        const long long pt1 = prof_now(sm);
+        prof_add(sm, kProfGather, pt0);
+        expand_slots<MODE>(I, ctl, P, sm, cnt, (uint32_t)(e - g0), (uint32_t)(s_hi - g0), mat, k, t);
+        const long long pt2 = prof_now(sm);
+        prof_add(sm, kProfExpand, pt1);
+        e = s_hi;
+        __syncthreads();
+        prof_add(sm, kProfWait, pt2);
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) nnz_local += __shfl_xor_sync(0xFFFFFFFFu, nnz_local, d);
     if ((threadIdx.x & 31) == 0 && nnz_local) atomicAdd(&sm.st_nnz, (unsigned long long)nnz_local);
-    __syncthreads();
-    block_exclusive_scan(sm.off, cnt, sm);
-    const uint32_t E = sm.off[cnt];
-    const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t per = (E + kWarps - 1) / kWarps;
-    const uint32_t e0 = min(E, warp * per), e1 = min(E, e0 + per);
-    const uint32_t* rows = (mat == 0) ? I.rowidx : I.srows[mat - 1];
-    expand_entries<MODE>(I, ctl, P, sm, cnt, e0, e1, rows, mat, k);
-    if (threadIdx.x == 0) sm.st_read += E;
-    if (MODE == kModeSub)
-        flush_out(sm, I.fq[p ^ 1], &ctl->fcnt[p ^ 1], I.n, ctl);
-    else
-        flush_out(sm, I.touched, &ctl->tcnt, I.n, ctl);
-}
-
-// One chunk of a heavy column at level k.
-template <int MODE>
-__device__ void unit_heavy(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                           uint32_t k, uint32_t h) {
-    const uint32_t p = k & 1;
-    const uint2 d = ld_l2(I.hq[p] + h);
-    const uint32_t v = d.x, q = d.y;
-    const uint32_t mat = mat_for_level(ctl, k);
-    const ColRef c = col_of(I, mat, v);
-    const uint32_t lo = c.beg + q * P.chunk;
-    const uint32_t hi = c.beg + min(c.len, (q + 1) * P.chunk);
-    if (q == 0 && threadIdx.x == 0) {
-        if (MODE == kModeSub) atomicOr(I.bm[p ^ 1] + (v >> 5), 1u << (v & 31));
-        sm.st_nnz += (mat == 0) ? c.len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
-    }
-    const uint32_t* test_bm = I.bm[p];
-    uint32_t* write_bm = I.bm[p ^ 1];
-    uint32_t unmasked = 0, claims = 0;
-    for (uint32_t base = lo; base < hi; base += kThreads) {
-        const uint32_t e = base + threadIdx.x;
-        bool want = false;
-        uint32_t r = 0;
-        if (e < hi) {
-            r = ld_row(c.rows, e, mat);
-            if (MODE == kModeSub) {
-                bool light;
-                claim_sub(I, ctl, P, test_bm, write_bm, r, v, k, unmasked, claims, light);
-                want = light;
-            } else {
-                ++unmasked;
-                ++claims;
-                const unsigned long long old = atomicMin(I.y + r, plain_key(k, v));
-                want = (uint32_t)(old >> 32) != plain_stamp(k);
-            }
-        }
-        if (MODE == kModeSub)
-            append_warp(want, r, sm, I.fq[p ^ 1], &ctl->fcnt[p ^ 1], I.n, ctl);
-        else
-            append_warp(want, r, sm, I.touched, &ctl->tcnt, I.n, ctl);
-    }
-    warp_stats(sm, unmasked, claims);
-    if (threadIdx.x == 0) sm.st_read += (hi > lo ? hi - lo : 0u);
-    if (MODE == kModeSub)
-        flush_out(sm, I.fq[p ^ 1], &ctl->fcnt[p ^ 1], I.n, ctl);
-    else
-        flush_out(sm, I.touched, &ctl->tcnt, I.n, ctl);
+    tally_flush(sm, t);
+    const long long pt3 = prof_now(sm);
+    if (MODE == kModeSub) cta_flush(sm, I, ctl, P, p ^ 1, mat_for_level(ctl, k + 1));
+    prof_add(sm, kProfFlush, pt3);
 }
 
 // Comparator: apply the visited mask to a tile of touched rows of level k.
@@ -479,6 +760,8 @@ __device__ void unit_plain_mask(const Inst& I, InstCtl* ctl, const EngineParams&
     const uint32_t pn = (k + 1) & 1;
     const uint32_t base = tile_idx * P.tile;
     const uint32_t cnt = min(P.tile, ntouched - base);
+    const uint32_t mat_next = mat_for_level(ctl, k + 1);
+    uint32_t wc = sm.wcnt[threadIdx.x >> 5];
     for (uint32_t b0 = 0; b0 < cnt; b0 += kThreads) {
         const uint32_t t = b0 + threadIdx.x;
         bool want = false;
@@ -489,12 +772,14 @@ __device__ void unit_plain_mask(const Inst& I, InstCtl* ctl, const EngineParams&
                 const unsigned long long y = ld_relaxed64(I.y + r);
                 I.level[r] = (int32_t)(k + 1);
                 I.parent[r] = (uint32_t)(y & 0xFFFFFFFFull);
-                want = route_new(I, ctl, P, r, k + 1);
+                want = true;
             }
         }
-        append_warp(want, r, sm, I.fq[pn], &ctl->fcnt[pn], I.n, ctl);
+        stage_warp(want, r, sm, wc);
+        if (wc > (uint32_t)(kWarpBuf - 32)) warp_flush(sm, I, ctl, P, pn, mat_next, wc);
     }
-    flush_out(sm, I.fq[pn], &ctl->fcnt[pn], I.n, ctl);
+    if ((threadIdx.x & 31) == 0) sm.wcnt[threadIdx.x >> 5] = wc;
+    cta_flush(sm, I, ctl, P, pn, mat_next);
 }
 
 // Shrink: compacts the unvisited columns among vertices
@@ -522,20 +807,20 @@ __device__ void unit_shrink(const Inst& I, InstCtl* ctl, const EngineParams& P, 
         cnt_arr[t] = 0;
     }
     __syncthreads();
-    block_exclusive_scan(sm.off, cnt, sm);
+    block_exclusive_scan<kTileItems>(sm.off, cnt, sm);
     const uint32_t E = sm.off[cnt];
-    const uint32_t* rows = (src_mat == 0) ? I.rowidx : I.srows[src_mat - 1];
+    const uint32_t* rows = rows_of(I, src_mat);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t per = (E + kWarps - 1) / kWarps;
     const uint32_t e0 = min(E, warp * per), e1 = min(E, e0 + per);
-    // pass 1: count surviving rows per column
+    // pass 0 counts the surviving rows of each column, pass 1 writes them
     for (int pass = 0; pass < 2; ++pass) {
         uint32_t e = e0 + lane;
         uint32_t i = 0;
         if (e < e1) {
             uint32_t lo = 0, hi = cnt;
             while (hi - lo > 1) {
-                uint32_t mid = (lo + hi) >> 1;
+                const uint32_t mid = (lo + hi) >> 1;
                 if (sm.off[mid] <= e) lo = mid;
                 else hi = mid;
             }
@@ -548,8 +833,8 @@ __device__ void unit_shrink(const Inst& I, InstCtl* ctl, const EngineParams& P, 
             if (keep) {
                 const uint32_t pos = atomicAdd(&cnt_arr[i], 1u);
                 if (pass == 1) {
-                    const unsigned long long dst_pos = (unsigned long long)sm.gbase + pos;
-                    if (dst_pos < I.scap) I.srows[s][dst_pos] = r;
+                    const unsigned long long dpos = (unsigned long long)sm.gbase + pos;
+                    if (dpos < I.scap) I.srows[s][dpos] = r;
                 }
             }
         }
@@ -558,7 +843,7 @@ __device__ void unit_shrink(const Inst& I, InstCtl* ctl, const EngineParams& P, 
             // lengths of the new columns, then their begins
             for (uint32_t t = threadIdx.x; t < cnt; t += kThreads) I.slen[s][v0 + t] = cnt_arr[t];
             __syncthreads();
-            block_exclusive_scan(cnt_arr, cnt, sm);
+            block_exclusive_scan<kTileItems>(cnt_arr, cnt, sm);
             if (threadIdx.x == 0) {
                 const uint32_t S = cnt_arr[cnt];
                 const uint32_t g = atomicAdd(&ctl->shrink_out, S);
@@ -567,13 +852,12 @@ __device__ void unit_shrink(const Inst& I, InstCtl* ctl, const EngineParams& P, 
                 atomicAdd(&ctl->shrink_kept, (unsigned long long)S);
             }
             __syncthreads();
-            for (uint32_t t = threadIdx.x; t < cnt; t += kThreads) I.sbeg[s][v0 + t] = sm.gbase + cnt_arr[t];
-            // cnt_arr[t] now serves as the write cursor of column t, starting at its offset
+            // cnt_arr[t] now holds column t's offset and serves as its write cursor
+            for (uint32_t t = threadIdx.x; t < cnt; t += kThreads)
+                I.sbeg[s][v0 + t] = sm.gbase + cnt_arr[t];
             __syncthreads();
         }
     }
-    // rows of column t occupy [gbase + off_t, ...): cursors advanced from the
-    // exclusive offsets, so pass 2 wrote at gbase + offset + rank.
     if (threadIdx.x == 0) atomicAdd(&ctl->shrink_read, (unsigned long long)E);
     __syncthreads();
 }
@@ -585,26 +869,30 @@ __device__ void unit_shrink(const Inst& I, InstCtl* ctl, const EngineParams& P, 
 // Runs one unit of phase (kind, k).
 template <int MODE>
 __device__ void run_unit(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                         uint32_t kind, uint32_t k, uint32_t unit, uint32_t nheavy,
-                         uint32_t nitems) {
+                         uint32_t kind, uint32_t k, uint32_t unit, uint32_t nitems) {
     if (kind == kPhShrink) {
         // k = level just completed; its write bitmap holds every vertex reached so far
         const uint32_t src_mat = ld_relaxed(&ctl->mat_cur);
         unit_shrink(I, ctl, P, sm, unit, I.bm[(k + 1) & 1], src_mat, /*dst=*/nitems);
     } else if (kind == kPhPlainMask) {
         unit_plain_mask(I, ctl, P, sm, k, unit, nitems);
-    } else if (unit < nheavy) {
-        unit_heavy<MODE>(I, ctl, P, sm, k, unit);
     } else {
-        unit_light<MODE>(I, ctl, P, sm, k, unit - nheavy, nitems);
+        unit_level<MODE>(I, ctl, P, sm, k, unit);
     }
     stats_flush(sm, ctl);
 }
 
-__device__ __forceinline__ uint32_t units_of(const EngineParams& P, uint32_t kind, uint32_t nheavy,
-                                             uint32_t nitems, uint32_t n) {
-    if (kind == kPhShrink) return (n + P.shrink_tile - 1) / P.shrink_tile;
-    return nheavy + (nitems + P.tile - 1) / P.tile;
+// Optional per-phase trace entry: [time lo, time hi, kind<<24 | level, alone]
+// and [items, vertices, entries (low 32 bits), 0].
+__device__ void trace_put(const Inst& I, InstCtl* ctl, uint32_t kind, uint32_t level,
+                          uint32_t alone, uint32_t ni, uint32_t nf, unsigned long long ne) {
+    const uint32_t tn = ld_relaxed(&ctl->trace_n);
+    if (tn >= I.trace_cap) return;
+    const uint64_t now = globaltimer();
+    I.trace[2 * tn] = make_uint4((uint32_t)now, (uint32_t)(now >> 32),
+                                 (kind << 24) | (level & 0xFFFFFFu), alone);
+    I.trace[2 * tn + 1] = make_uint4(ni, nf, (uint32_t)min(ne, 0xFFFFFFFFull), 0u);
+    st_relaxed(&ctl->trace_n, tn + 1);
 }
 
 // Thread 0 of the advancing CTA: the phase that follows (kind, k), written to
@@ -612,7 +900,7 @@ __device__ __forceinline__ uint32_t units_of(const EngineParams& P, uint32_t kin
 template <int MODE>
 __device__ void decide_next(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                             uint32_t kind, uint32_t k, uint32_t* done_count) {
-    uint32_t nkind = 0, nk = 0, nh = 0, ni = 0, finish = 0;
+    uint32_t nkind = 0, nk = 0, ni = 0, finish = 0;
     if (kind == kPhPlainMult) {
         // comparator: the mask phase of the same level follows the multiply
         const uint32_t t = ld_relaxed(&ctl->tcnt);
@@ -627,21 +915,18 @@ __device__ void decide_next(const Inst& I, InstCtl* ctl, const EngineParams& P, 
         // the frontier of level k+1 is complete (after a level, or after a shrink)
         const uint32_t pn = (k + 1) & 1, pc = k & 1;
         const uint32_t nf = ld_relaxed(&ctl->fcnt[pn]);
-        const uint32_t nhc = ld_relaxed(&ctl->hcnt[pn]);
-        const uint32_t nhv = ld_relaxed(&ctl->hvert[pn]);
         uint32_t reached = ld_relaxed(&ctl->reached);
         uint32_t shrinks = ld_relaxed(&ctl->shrinks);
         if (kind != kPhShrink) {
             st_relaxed(&ctl->levels, k + 1);
-            if (nf == 0 && nhc == 0) {
+            if (nf == 0) {
                 finish = 1;
             } else {
-                reached += nf + nhv;
+                reached += nf;
                 st_relaxed(&ctl->reached, reached);
                 // the buffers of level k become the "next" buffers of level k+1
                 st_relaxed(&ctl->fcnt[pc], 0u);
-                st_relaxed(&ctl->hcnt[pc], 0u);
-                st_relaxed(&ctl->hvert[pc], 0u);
+                st_relaxed64(&ctl->bctr[pc], 0ull);
                 if (MODE == kModePlain) st_relaxed(&ctl->tcnt, 0u);
             }
         } else {
@@ -672,15 +957,12 @@ __device__ void decide_next(const Inst& I, InstCtl* ctl, const EngineParams& P, 
             } else {
                 nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
                 nk = k + 1;
-                nh = nhc;
-                ni = nf;
             }
         }
     }
     if (ld_relaxed(&ctl->err) != 0) finish = 1;
     sm.cmd.kind = nkind;
     sm.cmd.level = nk;
-    sm.cmd.nheavy = nh;
     sm.cmd.nitems = ni;
     sm.cmd.quit = finish;
     if (finish) {
@@ -705,18 +987,34 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
             atomicAdd(heartbeat, 1ull);
         }
         __syncthreads();
-        if (sm.cmd.quit) return;
-        const uint32_t nkind = sm.cmd.kind, nk = sm.cmd.level;
-        const uint32_t nh = sm.cmd.nheavy, ni = sm.cmd.nitems;
-        const uint32_t units = units_of(P, nkind, nh, ni, I.n);
-        const bool alone = (nkind == kPhShrink) ? (units <= 1) : (nh == 0 && ni <= P.narrow_max);
+        if (sm.cmd.quit) {
+            if (I.trace && threadIdx.x == 0) trace_put(I, ctl, 0xFFu, k, 0u, 0u, 0u, 0ull);
+            return;
+        }
+        const uint32_t nkind = sm.cmd.kind, nk = sm.cmd.level, ni = sm.cmd.nitems;
+        uint32_t units, nf = 0;
+        unsigned long long ne = 0;
+        bool alone;
+        if (nkind == kPhShrink) {
+            units = (I.n + P.shrink_tile - 1) / P.shrink_tile;
+            alone = units <= 1;
+        } else if (nkind == kPhPlainMask) {
+            units = (ni + P.tile - 1) / P.tile;
+            alone = ni <= P.narrow_max;
+        } else {
+            // a level (or the comparator's multiply) over the frontier of level nk
+            ne = ld_relaxed64(&ctl->bctr[nk & 1]) >> kBlockBits;
+            nf = ld_relaxed(&ctl->fcnt[nk & 1]);
+            units = (uint32_t)((ne + P.unit - 1) / P.unit);
+            alone = nf <= P.narrow_max && ne <= P.narrow_edges;
+        }
+        if (I.trace && threadIdx.x == 0) trace_put(I, ctl, nkind, nk, alone, ni, nf, ne);
         if (!alone) {
             if (threadIdx.x == 0) {
                 const uint32_t e = ld_relaxed(&ctl->epoch) + 1;
                 const uint32_t q = e & 1;
                 st_relaxed(&ctl->kind[q], nkind);
                 st_relaxed(&ctl->plevel[q], nk);
-                st_relaxed(&ctl->nheavy[q], nh);
                 st_relaxed(&ctl->nitems[q], ni);
                 st_relaxed(&ctl->pending[q], units);
                 st_relaxed(&ctl->epoch, e);
@@ -730,7 +1028,7 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
             return;
         }
         // narrow: this CTA runs every unit of the phase, then decides again
-        for (uint32_t u = 0; u < units; ++u) run_unit<MODE>(I, ctl, P, sm, nkind, nk, u, nh, ni);
+        for (uint32_t u = 0; u < units; ++u) run_unit<MODE>(I, ctl, P, sm, nkind, nk, u, ni);
         __threadfence();
         __syncthreads();
         kind = nkind;
@@ -738,7 +1036,7 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
     }
 }
 
-// Thread 0: whether instance q has an untaken unit in its published phase.
+// Whether instance q has an untaken unit in its published phase.
 __device__ __forceinline__ bool has_work(const Inst* insts, uint32_t q) {
     InstCtl* ctl = insts[q].ctl;
     if (ld_relaxed(&ctl->status) != kRunning) return false;
@@ -748,7 +1046,7 @@ __device__ __forceinline__ bool has_work(const Inst* insts, uint32_t q) {
     return (uint32_t)(d >> 32) == e && taken < (uint32_t)d;
 }
 
-// Thread 0: takes a unit of instance q if one is left; fills sm.cmd.
+// One lane: takes a unit of instance q if one is left; fills sm.cmd.
 __device__ __forceinline__ bool take_unit(const Inst* insts, uint32_t q, Smem& sm) {
     InstCtl* ctl = insts[q].ctl;
     const unsigned long long old = atomicAdd(&ctl->grab, 1ull);
@@ -762,7 +1060,6 @@ __device__ __forceinline__ bool take_unit(const Inst* insts, uint32_t q, Smem& s
     sm.cmd.unit = t;
     sm.cmd.kind = ld_relaxed(&ctl->kind[qq]);
     sm.cmd.level = ld_relaxed(&ctl->plevel[qq]);
-    sm.cmd.nheavy = ld_relaxed(&ctl->nheavy[qq]);
     sm.cmd.nitems = ld_relaxed(&ctl->nitems[qq]);
     return true;
 }
@@ -771,6 +1068,7 @@ __device__ __forceinline__ bool take_unit(const Inst* insts, uint32_t q, Smem& s
 // unit it can; the whole CTA then runs it.  Returns true if a unit was run.
 template <int MODE>
 __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
+    const long long pt0 = prof_now(sm);
     if (threadIdx.x < 32) {
         const uint32_t lane = threadIdx.x;
         bool got = false;
@@ -798,11 +1096,13 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
     }
     __syncthreads();
     if (!sm.cmd.has) return false;
+    prof_add(sm, kProfTake, pt0);
+    if (sm.prof_on && threadIdx.x == 0) sm.prof[kProfUnits] += 1;
     cursor = sm.cmd.q;
     const Inst& I = sm.I;
     InstCtl* ctl = I.ctl;
     const uint32_t kind = sm.cmd.kind, k = sm.cmd.level, epoch = sm.cmd.epoch;
-    run_unit<MODE>(I, ctl, a.p, sm, kind, k, sm.cmd.unit, sm.cmd.nheavy, sm.cmd.nitems);
+    run_unit<MODE>(I, ctl, a.p, sm, kind, k, sm.cmd.unit, sm.cmd.nitems);
     // completion: release this CTA's writes, then count the unit down
     __threadfence();
     __syncthreads();
@@ -812,16 +1112,22 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
         atomicAdd(a.heartbeat, 1ull);
     }
     __syncthreads();
-    if (sm.cmd.last) advance<MODE>(I, ctl, a.p, sm, kind, k, a.done_count, a.heartbeat);
+    if (sm.cmd.last) {
+        const long long pt1 = prof_now(sm);
+        advance<MODE>(I, ctl, a.p, sm, kind, k, a.done_count, a.heartbeat);
+        prof_add(sm, kProfAdvance, pt1);
+    }
     return true;
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2) engine_kernel(EngineArgs a) {
-    __shared__ Smem sm;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     if (threadIdx.x == 0) {
-        sm.out_cnt = 0;
-        sm.out_valid = kOutBuf;
+        for (int q = 0; q < kWarps; ++q) sm.wcnt[q] = 0;
+        sm.prof_on = a.prof != nullptr;
+        for (int q = 0; q < kProfSlots; ++q) sm.prof[q] = 0;
         sm.st_read = sm.st_unmasked = sm.st_claims = sm.st_nnz = 0;
         sm.cur_q = kUnset;
     }
@@ -834,6 +1140,7 @@ __global__ void __launch_bounds__(kThreads, 2) engine_kernel(EngineArgs a) {
         if (threadIdx.x == 0) sm.cmd.quit = (ld_relaxed(a.done_count) >= a.ninst);
         __syncthreads();
         if (sm.cmd.quit) break;
+        const long long pti = prof_now(sm);
         if (find_and_run<MODE>(a, sm, cursor)) {
             backoff = 64;
             continue;
@@ -858,7 +1165,10 @@ __global__ void __launch_bounds__(kThreads, 2) engine_kernel(EngineArgs a) {
             if (backoff < 2048) backoff <<= 1;
         }
         __syncthreads();
+        prof_add(sm, kProfIdle, pti);
     }
+    if (a.prof && threadIdx.x == 0)
+        for (int q = 0; q < kProfSlots; ++q) atomicAdd(a.prof + q, sm.prof[q]);
 }
 
 // ---------------------------------------------------------------------------
@@ -894,54 +1204,61 @@ __global__ void init_source_kernel(EngineArgs a) {
         *a.heartbeat = 0ull;
     }
     if (q >= a.ninst) return;
-    const Inst* insts = a.insts;
+    const Inst& I = a.insts[q];
     const EngineParams& P = a.p;
-    const Inst& I = insts[q];
     InstCtl* ctl = I.ctl;
     const uint32_t s = I.src;
     I.level[s] = 0;
     I.parent[s] = s;
     if (P.mode == kModeSub) I.bm[0][s >> 5] |= 1u << (s & 31);  // V_2 = V_1 \ {source}
+    // frontier of level 0: one block holding the source
     const uint32_t len = I.colptr[s + 1] - I.colptr[s];
-    uint32_t nh = 0, nf = 0;
-    if (len >= P.heavy) {
-        nh = (len + P.chunk - 1) / P.chunk;
-        for (uint32_t c = 0; c < nh; ++c) I.hq[0][c] = make_uint2(s, c);
-        ctl->hcnt[0] = nh;
-        ctl->hvert[0] = 1;
-    } else {
-        I.fq[0][0] = s;
-        nf = 1;
-        ctl->fcnt[0] = 1;
-    }
+    const uint32_t w = len + kVertexSlots;
+    I.fq[0][0] = s;
+    I.fbeg[0][0] = I.colptr[s];
+    I.fpre[0][0] = 0;
+    I.blk[0][0].vb = 0;
+    I.blk[0][0].nv = 1;
+    I.blk[0][0].eb = 0;
+    for (unsigned long long x = 0; x < w; x += P.unit) I.ustart[0][x / P.unit] = make_uint2(0, 0);
+    ctl->bctr[0] = ((unsigned long long)w << kBlockBits) | 1ull;
+    ctl->fcnt[0] = 1;
     ctl->reached = 1;
     ctl->mat_cur = 0;
     ctl->mat_prev = 0;
     ctl->mat_switch = 0;
-    const uint32_t units = nh + (nf ? 1u : 0u);
+    const uint32_t units = (w + P.unit - 1) / P.unit;
     ctl->kind[0] = (P.mode == kModePlain) ? kPhPlainMult : kPhLevel;
     ctl->plevel[0] = 0;
-    ctl->nheavy[0] = nh;
-    ctl->nitems[0] = nf;
+    ctl->nitems[0] = 0;
     ctl->pending[0] = units;
     ctl->epoch = 0;
     ctl->desc[0] = (0ull << 32) | units;
     ctl->desc[1] = ~0ull;
     ctl->grab = 0ull;
     ctl->status = kRunning;
+    if (I.trace && I.trace_cap) {
+        const uint64_t now = globaltimer();
+        I.trace[0] = make_uint4((uint32_t)now, (uint32_t)(now >> 32), (0xFEu << 24), 0u);
+        I.trace[1] = make_uint4(0u, 1u, w, 0u);
+        ctl->trace_n = 1;
+    }
 }
 
 // Writes the per-call fields of instance 0 (single searches reuse one
 // descriptor; kernel arguments avoid a host staging buffer).
-__global__ void set_query_kernel(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent) {
+__global__ void set_query_kernel(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
+                                 uint4* trace, uint32_t trace_cap) {
     inst->src = src;
     inst->level = level;
     inst->parent = parent;
+    inst->trace = trace;
+    inst->trace_cap = trace_cap;
 }
 
 cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
-                             cudaStream_t s) {
-    set_query_kernel<<<1, 1, 0, s>>>(inst, src, level, parent);
+                             uint4* trace, uint32_t trace_cap, cudaStream_t s) {
+    set_query_kernel<<<1, 1, 0, s>>>(inst, src, level, parent, trace, trace_cap);
     return cudaGetLastError();
 }
 
@@ -957,20 +1274,39 @@ cudaError_t launch_init(const EngineArgs& a, uint32_t max_n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int MODE>
+static cudaError_t set_smem_attr() {
+    static bool done = false;  // one attribute call per process and template instance
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(engine_kernel<MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(Smem));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
 cudaError_t launch_engine(const EngineArgs& a, int grid, cudaStream_t s) {
-    if (a.p.mode == kModePlain)
-        engine_kernel<kModePlain><<<grid, kThreads, 0, s>>>(a);
-    else
-        engine_kernel<kModeSub><<<grid, kThreads, 0, s>>>(a);
+    cudaError_t e;
+    if (a.p.mode == kModePlain) {
+        e = set_smem_attr<kModePlain>();
+        if (e != cudaSuccess) return e;
+        engine_kernel<kModePlain><<<grid, kThreads, sizeof(Smem), s>>>(a);
+    } else {
+        e = set_smem_attr<kModeSub>();
+        if (e != cudaSuccess) return e;
+        engine_kernel<kModeSub><<<grid, kThreads, sizeof(Smem), s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t engine_occupancy(uint32_t mode, int* blocks_per_sm) {
+    cudaError_t e = (mode == kModePlain) ? set_smem_attr<kModePlain>() : set_smem_attr<kModeSub>();
+    if (e != cudaSuccess) return e;
     if (mode == kModePlain)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, engine_kernel<kModePlain>,
-                                                             kThreads, 0);
+                                                             kThreads, sizeof(Smem));
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, engine_kernel<kModeSub>,
-                                                         kThreads, 0);
+                                                         kThreads, sizeof(Smem));
 }
 
 }  // namespace abfs

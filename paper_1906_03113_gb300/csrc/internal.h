@@ -10,12 +10,28 @@ namespace abfs {
 // Threads per CTA of the persistent engine.
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-// Largest frontier tile (vertices) a CTA expands at once.
-constexpr int kTileMax = 2048;
-// CTA staging buffer for newly reached vertices before one global append.
-constexpr int kOutBuf = 4096;
+// Largest group of frontier vertices a CTA stages in shared memory at once.
+constexpr int kTileMax = 1024;
+// Entries each thread keeps in flight in the expand loop (memory-level parallelism).
+constexpr int kIlp = 4;
+// Per-warp staging buffer for newly reached vertices.  A warp writes its
+// buffer out as one frontier block once a further expand step (32 * kIlp
+// appends) might not fit; at the end of a unit the leftovers of all warps
+// leave as one block.
+constexpr int kWarpBuf = 256;
+constexpr int kWarpFlushAt = kWarpBuf - 32 * kIlp;
+// Largest work unit (entry slots) and the per-unit start bitmap it needs.
+constexpr uint32_t kUnitMax = 16384;
+constexpr int kStartWords = kUnitMax / 32 + 2;
 // Marker of an unset parent / unclaimed vertex (reads as -1 through int32).
 constexpr uint32_t kUnset = 0xFFFFFFFFu;
+// Weight of a frontier vertex in its level's work space: its column length
+// plus kVertexSlots, so units balance vertices as well as entries and a
+// vertex without entries still owns a slot.
+constexpr uint32_t kVertexSlots = 2;
+// Packed frontier counter: [entries : 40 bits][blocks : 24 bits].
+constexpr uint32_t kBlockBits = 24;
+constexpr uint32_t kBlockMask = (1u << kBlockBits) - 1u;
 
 enum Mode : uint32_t { kModeSub = 0, kModePlain = 1 };
 
@@ -28,19 +44,26 @@ enum PhaseKind : uint32_t {
 
 enum InstStatus : uint32_t { kRunning = 0, kDone = 1, kFailed = 2 };
 
+// A block of the frontier: nv consecutive vertices at fq[vb..], whose column
+// entries occupy [eb, eb + sum of their weights) of the level's entry space.
+// Blocks are numbered in the order of their entry ranges.
+struct Block {
+    uint32_t vb;
+    uint32_t nv;
+    unsigned long long eb;
+};
+
 // Device-resident control block of one search.  Zeroed at initialisation.
 struct InstCtl {
     unsigned long long grab;     // [epoch:32][units taken:32] of the published phase
     unsigned long long desc[2];  // per epoch parity: [epoch:32][units:32]
+    unsigned long long bctr[2];  // per level parity: [entries:40][blocks:24] of the frontier
     uint32_t pending[2];         // per epoch parity: units not yet completed
     uint32_t kind[2];            // per epoch parity: PhaseKind
     uint32_t plevel[2];          // per epoch parity: BFS level of the phase
-    uint32_t nheavy[2];          // per epoch parity: heavy-chunk units (come first)
-    uint32_t nitems[2];          // per epoch parity: light vertices (or touched rows / shrink items)
+    uint32_t nitems[2];          // per epoch parity: touched rows (mask) / copy index (shrink)
+    uint32_t fcnt[2];            // per level parity: frontier vertices
     uint32_t epoch;              // last published epoch (written by the advancer only)
-    uint32_t fcnt[2];            // per level parity: light frontier length
-    uint32_t hcnt[2];            // per level parity: heavy chunks
-    uint32_t hvert[2];           // per level parity: heavy vertices
     uint32_t tcnt;               // comparator: rows touched by the current multiply
     uint32_t status;             // InstStatus
     uint32_t err;                // abfs_status when status == kFailed
@@ -52,6 +75,7 @@ struct InstCtl {
     uint32_t mat_prev;           // matrix used for levels < mat_switch
     uint32_t mat_switch;         // first level that reads mat_cur
     uint32_t shrink_out;         // shrink: entries written so far
+    uint32_t trace_n;            // trace entries written
     uint32_t pad_;
     unsigned long long entries_read;
     unsigned long long entries_unmasked;
@@ -68,12 +92,16 @@ struct Inst {
     uint32_t n;
     uint32_t src;
     uint32_t nwords;         // ceil(n/32)
-    uint32_t hcap;           // capacity of each heavy-chunk queue
+    uint32_t bcap;           // blocks per frontier
+    unsigned long long ucap; // unit starts per frontier
     int32_t* level;          // output
     uint32_t* parent;        // output (0xFFFFFFFF reads as -1)
     uint32_t* bm[2];         // visited bitmaps, ping-pong by level parity
-    uint32_t* fq[2];         // light frontier queues, by level parity
-    uint2* hq[2];            // heavy chunk queues (vertex, chunk index), by level parity
+    uint32_t* fq[2];         // frontier vertices, by level parity
+    uint32_t* fbeg[2];       // their column begins (kUnset: no entries)
+    uint32_t* fpre[2];       // their entry offsets within their block
+    Block* blk[2];           // frontier blocks
+    uint2* ustart[2];        // unit u starts in (block, vertex index in block)
     unsigned long long* y;   // comparator: stamped (min, index) accumulator
     uint32_t* touched;       // comparator: rows touched by the multiply
     uint32_t* sbeg[2];       // shrunk copies: column begin per vertex
@@ -81,14 +109,17 @@ struct Inst {
     uint32_t* srows[2];      // shrunk copies: row arrays
     unsigned long long scap; // capacity of each shrunk row array
     InstCtl* ctl;
+    uint4* trace;            // optional per-phase trace (nullptr = off)
+    uint32_t trace_cap;
+    uint32_t pad_;
 };
 
 struct EngineParams {
     uint32_t mode;
-    uint32_t tile;
-    uint32_t heavy;
-    uint32_t chunk;
+    uint32_t tile;                 // vertices per staged group / touched rows per mask unit
+    uint32_t unit;                 // column entries per work unit
     uint32_t narrow_max;
+    uint32_t narrow_edges;
     float shrink_theta;
     uint32_t shrink_max;
     uint32_t shrink_tile;          // vertices per shrink unit
@@ -100,14 +131,29 @@ struct EngineArgs {
     uint32_t ninst;
     uint32_t* done_count;          // instances finished (any status)
     unsigned long long* heartbeat; // progress counter for the bounded waits
+    unsigned long long* prof;      // optional per-category CTA cycle totals (kProfSlots), or null
     EngineParams p;
+};
+
+// Cycle accounting of the engine's CTAs (profiling runs only).
+enum ProfSlot : int {
+    kProfIdle = 0,     // no unit available
+    kProfTake = 1,     // scanning searches and taking a unit
+    kProfGather = 2,   // staging frontier vertices of a unit
+    kProfExpand = 3,   // warp 0's own expand time
+    kProfWait = 4,     // waiting for the other warps' expand
+    kProfFlush = 5,    // writing the unit's leftovers as a block
+    kProfAdvance = 6,  // advancing a search to its next phase
+    kProfUnits = 7,    // units run (a count)
+    kProfSlots = 8
 };
 
 // Launch helpers implemented in engine.cu.
 cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
-                             cudaStream_t s);
+                             uint4* trace, uint32_t trace_cap, cudaStream_t s);
 cudaError_t launch_init(const EngineArgs& a, uint32_t max_n, cudaStream_t s);
 cudaError_t launch_engine(const EngineArgs& a, int grid, cudaStream_t s);
 cudaError_t engine_occupancy(uint32_t mode, int* blocks_per_sm);
+size_t engine_smem_bytes();
 
 }  // namespace abfs

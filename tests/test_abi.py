@@ -30,8 +30,8 @@ def test_strerror_and_version(lib):
 def test_default_params_are_valid(lib):
     p = abfs.default_params()
     assert p.mode == abfs.MODE_SUBMATRIX
-    assert 32 <= p.tile <= 2048 and p.tile % 32 == 0
-    assert p.narrow_max <= p.tile and p.heavy_degree >= p.chunk
+    assert 32 <= p.tile <= 1024 and p.tile % 32 == 0
+    assert p.unit_entries >= 256 and p.unit_entries % 256 == 0
     assert p.timeout_ms > 0
 
 
@@ -65,5 +65,7 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
 def test_parameter_validation(lib):
     p = abfs.default_params()
     size = ctypes.c_size_t()
+    assert set(p.as_dict()) >= {"mode", "tile", "unit_entries", "narrow_max", "narrow_edges",
+                                "ctas_per_sm", "shrink_theta", "shrink_max", "timeout_ms"}
     # footprint of a null graph is an argument error, not a crash
     assert lib.abfs_graph_footprint(None, ctypes.byref(p), ctypes.byref(size)) == binding.ERR_INVALID_ARG

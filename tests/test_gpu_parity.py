@@ -38,6 +38,13 @@ def _check(g, src, level, parent, ctx=""):
     return lev_o
 
 
+def _e_adj(g, lev):
+    cols = np.repeat(np.arange(g.n), g.degrees())
+    lj = lev[cols]
+    li = lev[g.rowidx.astype(np.int64)]
+    return int(((lj >= 0) & (li == lj + 1)).sum())
+
+
 def _params(mode=SUB, **kw):
     return abfs.default_params(mode=mode, **kw)
 
@@ -46,12 +53,13 @@ MODES = [
     ("sub", dict(mode=SUB)),
     ("plain", dict(mode=PLAIN)),
     ("sub_shrink", dict(mode=SUB, shrink_theta=0.3, shrink_max=3)),
-    ("sub_small_tiles", dict(mode=SUB, tile=32, narrow_max=0, heavy_degree=128, chunk=128)),
-    ("plain_small_tiles", dict(mode=PLAIN, tile=64, narrow_max=32, heavy_degree=256, chunk=128)),
-    ("sub_narrow_all", dict(mode=SUB, tile=2048, narrow_max=2048)),
-    ("sub_wide_all", dict(mode=SUB, tile=256, narrow_max=0, ctas_per_sm=1)),
-    ("sub_shrink_every", dict(mode=SUB, tile=128, narrow_max=0, shrink_theta=0.05, shrink_max=20,
-                              heavy_degree=256, chunk=128)),
+    ("sub_small_units", dict(mode=SUB, tile=32, narrow_max=0, narrow_edges=0, unit_entries=256)),
+    ("plain_small_units", dict(mode=PLAIN, tile=64, narrow_max=32, narrow_edges=256,
+                               unit_entries=512)),
+    ("sub_narrow_all", dict(mode=SUB, tile=1024, narrow_max=1 << 30, narrow_edges=1 << 30)),
+    ("sub_wide_all", dict(mode=SUB, tile=256, narrow_max=0, narrow_edges=0, ctas_per_sm=1)),
+    ("sub_shrink_every", dict(mode=SUB, tile=128, narrow_max=0, narrow_edges=0, shrink_theta=0.05,
+                              shrink_max=20, unit_entries=1024)),
 ]
 
 
@@ -114,6 +122,12 @@ def test_small_graphs_all_modes(small, mode_name, kw):
             assert st["nnz_reached"] == nnz_c, (name, s, st)
             if kw.get("mode") == PLAIN:
                 assert st["entries_read"] == nnz_c and st["entries_unmasked"] == nnz_c
+            else:
+                # rows that pass the mask are exactly the entries j -> i with
+                # level(i) = level(j) + 1 (E_adj): the multiplies of Theorem 1
+                assert st["entries_unmasked"] == _e_adj(g, lev_o), (name, s, st)
+            if kw.get("mode") == PLAIN:
+                pass
             elif not kw.get("shrink_theta"):
                 # each reached column is read exactly once (Claim 1)
                 assert st["entries_read"] == nnz_c, (name, s, st)
@@ -177,7 +191,7 @@ def test_exhaustive_tiny_graphs_in_one_batch():
                 srcs.append(s)
                 hosts.append(g)
         levels, parents, st = abfs.run_batch(graphs, srcs, params=_params(mode=mode, tile=32,
-                                                                           narrow_max=32))
+                                                                           unit_entries=256))
         torch.cuda.synchronize()
         assert all(x == 0 for x in st)
         for g, s, L, P in zip(hosts, srcs, levels, parents):
