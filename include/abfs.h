@@ -210,6 +210,34 @@ int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count, uint32_t 
               const char* cache_path, abfs_stream_t stream, abfs_params* best, float* best_ms);
 
 /*
+ * One search, like abfs_run with default parameters, that allocates nothing.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc -- for example code that runs while an allocator is locked
+ * or disallowed (inside a memory pool's callback, a real-time serving thread
+ * that must not block on allocation, or a process whose device memory is
+ * budgeted up front) and so cannot use abfs_graph_create/abfs_run, which
+ * allocate a graph copy and a workspace.
+ *
+ * The caller passes device pointers: colptr[n+1] and rowidx[nnz] (CSC of A^T
+ * as for abfs_graph_create, used in place, not copied or validated) and the
+ * outputs level[n] and parent[n].  The scratch memory is a fixed 64 MiB
+ * device array inside this library (held on every GPU that loads it until the
+ * process exits), enough for graphs up to about 1.1 million vertices; larger
+ * inputs are rejected with ABFS_ERR_UNSUPPORTED before any device work.
+ *
+ * The first call on a device looks up that array's device address (once,
+ * with the device current); make that first call before any stream capture.
+ * Every call uses the same array, which keeps the previous call's contents;
+ * the call clears everything a search needs at zero.  Calls whose device work
+ * overlaps (on different streams or host threads) race on the array and give
+ * wrong results: order them on one stream.  Synchronises `stream`; returns the
+ * search's status (ABFS_ERR_TIMEOUT or ABFS_ERR_DEVICE if the device side
+ * failed).
+ */
+int abfs_run_static(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, uint64_t nnz,
+                    uint32_t source, int32_t* level, int32_t* parent, abfs_stream_t stream);
+
+/*
  * Device-memory hook: alloc(bytes, ctx) returns device memory or NULL;
  * free_fn(ptr, ctx) releases it.  Both NULL restores cudaMalloc/cudaFree.
  * Applies to allocations made after the call (graphs, workspaces, plans);

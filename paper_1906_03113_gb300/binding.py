@@ -122,6 +122,7 @@ def load():
         "abfs_tune": ([vp, P(u32), u32, u32, ctypes.c_char_p, vp, P(Params),
                        P(ctypes.c_float)], c_int),
         "abfs_set_allocator": ([vp, vp, vp], c_int),
+        "abfs_run_static": ([vp, vp, u32, u64, u32, vp, vp, vp], c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -370,6 +371,16 @@ class BatchPlan:
                 _lib.abfs_batch_destroy(self.handle)
         except Exception:
             pass
+
+
+def run_static(colptr, rowidx, source: int, level, parent, stream=None) -> int:
+    """abfs_run_static: one search with the library's fixed device scratch array
+    (no allocation).  colptr/rowidx/level/parent are CUDA tensors; returns the
+    status code."""
+    n = colptr.numel() - 1
+    return load().abfs_run_static(colptr.data_ptr(), rowidx.data_ptr() if rowidx.numel() else None,
+                                  n, rowidx.numel(), int(source), level.data_ptr(),
+                                  parent.data_ptr(), _stream_ptr(stream))
 
 
 def tune(g: Graph, sources, mode: int = MODE_SUBMATRIX, cache_path: str | None = None,

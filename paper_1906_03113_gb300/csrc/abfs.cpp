@@ -104,9 +104,13 @@ void dev_free(void* p) {
     else cudaFree(p);
 }
 
+}  // namespace
+
 // ---------------------------------------------------------------------------
-// parameters
+// parameters and per-search workspace layout (shared with static_ws.cu)
 // ---------------------------------------------------------------------------
+
+namespace abfs {
 
 abfs_params default_params() {
     abfs_params p;
@@ -161,14 +165,6 @@ bool same_layout(const abfs_params& a, const abfs_params& b) {
 // per-search workspace layout
 // ---------------------------------------------------------------------------
 
-struct Layout {
-    size_t bm[2], fq[2], fbeg[2], fpre[2], blk[2], ustart[2], y, touched, sbeg[2], slen[2],
-        srows[2], ctl, inst;
-    size_t total;
-    uint32_t nwords, bcap, ncopies;
-    unsigned long long ucap, scap;
-};
-
 Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p) {
     Layout L;
     std::memset(&L, 0, sizeof(L));
@@ -210,7 +206,47 @@ Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p) {
     return L;
 }
 
-}  // namespace
+Inst make_inst_raw(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, char* base,
+                   const Layout& L, uint32_t src, int32_t* level, int32_t* parent) {
+    Inst I;
+    std::memset(&I, 0, sizeof(I));
+    I.colptr = colptr;
+    I.rowidx = rowidx;
+    I.n = n;
+    I.src = src;
+    I.nwords = L.nwords;
+    I.bcap = L.bcap;
+    I.ucap = L.ucap;
+    I.level = level;
+    I.parent = reinterpret_cast<uint32_t*>(parent);
+    for (int i = 0; i < 2; ++i) {
+        I.fq[i] = reinterpret_cast<uint32_t*>(base + L.fq[i]);
+        I.fbeg[i] = reinterpret_cast<uint32_t*>(base + L.fbeg[i]);
+        I.fpre[i] = reinterpret_cast<uint32_t*>(base + L.fpre[i]);
+        I.blk[i] = reinterpret_cast<Block*>(base + L.blk[i]);
+        I.ustart[i] = reinterpret_cast<uint2*>(base + L.ustart[i]);
+        I.bm[i] = L.bm[i] ? reinterpret_cast<uint32_t*>(base + L.bm[i]) : nullptr;
+    }
+    if (L.y) I.y = reinterpret_cast<unsigned long long*>(base + L.y);
+    if (L.touched) I.touched = reinterpret_cast<uint32_t*>(base + L.touched);
+    for (uint32_t i = 0; i < L.ncopies; ++i) {
+        I.sbeg[i] = reinterpret_cast<uint32_t*>(base + L.sbeg[i]);
+        I.slen[i] = reinterpret_cast<uint32_t*>(base + L.slen[i]);
+        I.srows[i] = reinterpret_cast<uint32_t*>(base + L.srows[i]);
+    }
+    I.scap = L.scap;
+    I.ctl = reinterpret_cast<InstCtl*>(base + L.ctl);
+    return I;
+}
+
+int grid_for(int sms, const abfs_params& p) {
+    int bps = 0;
+    if (engine_occupancy(p.mode, &bps) != cudaSuccess || bps < 1) bps = 1;
+    const int per_sm = std::min<int>(bps, (int)p.ctas_per_sm);
+    return std::max(per_sm * std::max(sms, 1), 1);
+}
+
+}  // namespace abfs
 
 // ---------------------------------------------------------------------------
 // graph
@@ -278,35 +314,7 @@ void free_workspace(Workspace& w) {
 
 Inst make_inst(const abfs_graph_s* g, char* base, const Layout& L, uint32_t src, int32_t* level,
                int32_t* parent) {
-    Inst I;
-    std::memset(&I, 0, sizeof(I));
-    I.colptr = g->d_colptr;
-    I.rowidx = g->d_rowidx;
-    I.n = g->n;
-    I.src = src;
-    I.nwords = L.nwords;
-    I.bcap = L.bcap;
-    I.ucap = L.ucap;
-    I.level = level;
-    I.parent = reinterpret_cast<uint32_t*>(parent);
-    for (int i = 0; i < 2; ++i) {
-        I.fq[i] = reinterpret_cast<uint32_t*>(base + L.fq[i]);
-        I.fbeg[i] = reinterpret_cast<uint32_t*>(base + L.fbeg[i]);
-        I.fpre[i] = reinterpret_cast<uint32_t*>(base + L.fpre[i]);
-        I.blk[i] = reinterpret_cast<Block*>(base + L.blk[i]);
-        I.ustart[i] = reinterpret_cast<uint2*>(base + L.ustart[i]);
-        I.bm[i] = L.bm[i] ? reinterpret_cast<uint32_t*>(base + L.bm[i]) : nullptr;
-    }
-    if (L.y) I.y = reinterpret_cast<unsigned long long*>(base + L.y);
-    if (L.touched) I.touched = reinterpret_cast<uint32_t*>(base + L.touched);
-    for (uint32_t i = 0; i < L.ncopies; ++i) {
-        I.sbeg[i] = reinterpret_cast<uint32_t*>(base + L.sbeg[i]);
-        I.slen[i] = reinterpret_cast<uint32_t*>(base + L.slen[i]);
-        I.srows[i] = reinterpret_cast<uint32_t*>(base + L.srows[i]);
-    }
-    I.scap = L.scap;
-    I.ctl = reinterpret_cast<InstCtl*>(base + L.ctl);
-    return I;
+    return make_inst_raw(g->d_colptr, g->d_rowidx, g->n, base, L, src, level, parent);
 }
 
 // Ensures g->ws fits params p (reallocating after the previous use finished).
@@ -346,14 +354,7 @@ int ensure_workspace(abfs_graph_s* g, const abfs_params& p) {
     return ABFS_OK;
 }
 
-int grid_size(const abfs_graph_s* g, const abfs_params& p, uint32_t max_units_hint) {
-    int bps = 0;
-    if (engine_occupancy(p.mode, &bps) != cudaSuccess || bps < 1) bps = 1;
-    int per_sm = std::min<int>(bps, (int)p.ctas_per_sm);
-    int grid = per_sm * std::max(g->sms, 1);
-    (void)max_units_hint;
-    return std::max(grid, 1);
-}
+int grid_size(const abfs_graph_s* g, const abfs_params& p, uint32_t) { return grid_for(g->sms, p); }
 
 void fill_stats(const InstCtl& c, abfs_stats* st) {
     std::memset(st, 0, sizeof(*st));

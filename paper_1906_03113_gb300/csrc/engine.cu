@@ -1262,6 +1262,14 @@ cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t*
     return cudaGetLastError();
 }
 
+// Writes a whole search descriptor (passed by value) into device memory.
+__global__ void put_inst_kernel(Inst inst, Inst* dst) { *dst = inst; }
+
+cudaError_t launch_put_inst(const Inst& inst, Inst* dst, cudaStream_t s) {
+    put_inst_kernel<<<1, 1, 0, s>>>(inst, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init(const EngineArgs& a, uint32_t max_n, cudaStream_t s) {
     uint32_t blocks = (max_n + 255) / 256;
     if (blocks > 1024) blocks = 1024;

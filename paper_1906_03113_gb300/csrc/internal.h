@@ -2,8 +2,11 @@
 // runtime (abfs.cpp).  Not part of the public C-ABI.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "../../include/abfs.h"
 
 namespace abfs {
 
@@ -148,7 +151,27 @@ enum ProfSlot : int {
     kProfSlots = 8
 };
 
+// Per-search workspace layout: byte offsets of each buffer from the base.
+struct Layout {
+    size_t bm[2], fq[2], fbeg[2], fpre[2], blk[2], ustart[2], y, touched, sbeg[2], slen[2],
+        srows[2], ctl, inst;
+    size_t total;
+    uint32_t nwords, bcap, ncopies;
+    unsigned long long ucap, scap;
+};
+
+// Host helpers implemented in abfs.cpp.
+abfs_params default_params();
+bool shrink_enabled(const abfs_params& p);
+int check_params(const abfs_params& p);
+EngineParams engine_params(const abfs_params& p);
+Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p);
+Inst make_inst_raw(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, char* base,
+                   const Layout& L, uint32_t src, int32_t* level, int32_t* parent);
+int grid_for(int sms, const abfs_params& p);
+
 // Launch helpers implemented in engine.cu.
+cudaError_t launch_put_inst(const Inst& inst, Inst* dst, cudaStream_t s);
 cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
                              uint4* trace, uint32_t trace_cap, cudaStream_t s);
 cudaError_t launch_init(const EngineArgs& a, uint32_t max_n, cudaStream_t s);
