@@ -210,6 +210,63 @@ int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count, uint32_t 
               const char* cache_path, abfs_stream_t stream, abfs_params* best, float* best_ms);
 
 /*
+ * Serving: a long-lived device loop answers BFS queries on resident graphs
+ * (continuous batching).  Requests are queued by abfs_serve_submit; a host
+ * admission thread moves them into free device slots as soon as a slot and
+ * enough workspace memory (abfs_graph_footprint of the query's graph, carved
+ * from a memory budget) are free, while other queries are running; their
+ * work overlaps on the device in one persistent launch, which any CTA serves
+ * unit by unit.  The launch ends after idle_exit_ms without work and is
+ * relaunched on demand.  Each query's result equals abfs_run's, bit for bit.
+ * The paper has no counterpart (it evaluates single searches).
+ */
+typedef struct {
+    uint32_t max_slots;       /* queries on the device at once (1..4096) */
+    uint32_t queue_capacity;  /* queued requests beyond which submit returns ABFS_ERR_BUSY */
+    uint64_t memory_budget;   /* device bytes for query workspaces */
+    uint32_t idle_exit_ms;    /* the device loop ends after this long without work */
+    abfs_params params;       /* engine parameters of every query */
+} abfs_serve_cfg;
+
+typedef struct {
+    uint64_t submitted;       /* requests accepted by abfs_serve_submit */
+    uint64_t completed;       /* queries finished (any status) */
+    uint64_t failed;          /* queries that finished with a non-OK status */
+    uint64_t launches;        /* device loop launches */
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* submit -> done latency */
+    double wall_s;            /* abfs_serve_start -> abfs_serve_stop */
+    double qps;               /* completed / wall_s */
+} abfs_serve_report;
+
+/* Fills *cfg with defaults (256 slots, 16 GiB budget, 1M queue, 50 ms idle exit). */
+int abfs_serve_default_cfg(abfs_serve_cfg* cfg);
+
+/* Starts a server over ngraphs device-resident graphs (abfs_graph_create);
+ * the graphs must outlive it.  Allocates the slot table and the workspace
+ * budget up front.  cfg = NULL uses defaults. */
+int abfs_serve_start(const abfs_graph_t* g, uint32_t ngraphs, const abfs_serve_cfg* cfg,
+                     abfs_server_t* out);
+
+/* Queues one query: BFS on graph g[graph_idx] from `source`, results into the
+ * caller's DEVICE buffers level/parent (n int32 each), which must stay valid
+ * until the query is done.  Non-blocking; *ticket identifies the query.
+ * ABFS_ERR_BUSY when the queue is full, ABFS_ERR_INVALID_ARG on a bad graph
+ * index, source or buffer. */
+int abfs_serve_submit(abfs_server_t s, uint32_t graph_idx, uint32_t source, int32_t* level,
+                      int32_t* parent, uint64_t* ticket);
+
+/* *done = 1 and *status = the query's abfs_status once it finished, else
+ * *done = 0.  ABFS_ERR_NOT_FOUND for an unknown ticket. */
+int abfs_serve_poll(abfs_server_t s, uint64_t ticket, int* done, int32_t* status);
+
+/* Blocks until the query finished or timeout_ms passed (ABFS_ERR_TIMEOUT). */
+int abfs_serve_wait(abfs_server_t s, uint64_t ticket, uint32_t timeout_ms, int32_t* status);
+
+/* Finishes every queued and running query, ends the device loop, fills
+ * *report (may be NULL) and frees the server. */
+int abfs_serve_stop(abfs_server_t s, abfs_serve_report* report);
+
+/*
  * One search, like abfs_run with default parameters, that allocates nothing.
  * The paper has no counterpart: this entry point serves callers that cannot
  * call cudaMalloc -- for example code that runs while an allocator is locked

@@ -10,6 +10,9 @@ from .binding import (  # noqa: F401
     AbfsError,
     BatchPlan,
     Graph,
+    Server,
+    ServeCfg,
+    serve_default_cfg,
     Params,
     Stats,
     default_params,

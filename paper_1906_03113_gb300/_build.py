@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(obj)
     for f in cpp_files:
         obj = os.path.join(BUILD, f + ".o")
-        cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", *inc, "-c",
+        cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-pthread", *inc, "-c",
                os.path.join(CSRC, f), "-o", obj]
         jobs.append((cmd, obj))
         objs.append(obj)
@@ -85,7 +85,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("libabfs build failed:\n" + "\n".join(logs))
     tmp = LIB + ".tmp"
-    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-Xcompiler", "-pthread", "-o", tmp, *objs,
             "-Xlinker", "-rpath", "-Xlinker", os.path.join(cuda, "lib64")]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:

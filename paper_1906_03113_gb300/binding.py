@@ -71,6 +71,34 @@ class Stats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
 
 
+class ServeCfg(ctypes.Structure):
+    _fields_ = [
+        ("max_slots", ctypes.c_uint32),
+        ("queue_capacity", ctypes.c_uint32),
+        ("memory_budget", ctypes.c_uint64),
+        ("idle_exit_ms", ctypes.c_uint32),
+        ("params", Params),
+    ]
+
+
+class ServeReport(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64),
+        ("completed", ctypes.c_uint64),
+        ("failed", ctypes.c_uint64),
+        ("launches", ctypes.c_uint64),
+        ("p50_ms", ctypes.c_double),
+        ("p99_ms", ctypes.c_double),
+        ("mean_ms", ctypes.c_double),
+        ("max_ms", ctypes.c_double),
+        ("wall_s", ctypes.c_double),
+        ("qps", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class AbfsError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -123,6 +151,12 @@ def load():
                        P(ctypes.c_float)], c_int),
         "abfs_set_allocator": ([vp, vp, vp], c_int),
         "abfs_run_static": ([vp, vp, u32, u64, u32, vp, vp, vp], c_int),
+        "abfs_serve_default_cfg": ([P(ServeCfg)], c_int),
+        "abfs_serve_start": ([P(vp), u32, P(ServeCfg), P(vp)], c_int),
+        "abfs_serve_submit": ([vp, u32, u32, vp, vp, P(u64)], c_int),
+        "abfs_serve_poll": ([vp, u64, P(c_int), P(i32)], c_int),
+        "abfs_serve_wait": ([vp, u64, u32, P(i32)], c_int),
+        "abfs_serve_stop": ([vp, P(ServeReport)], c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -381,6 +415,63 @@ def run_static(colptr, rowidx, source: int, level, parent, stream=None) -> int:
     return load().abfs_run_static(colptr.data_ptr(), rowidx.data_ptr() if rowidx.numel() else None,
                                   n, rowidx.numel(), int(source), level.data_ptr(),
                                   parent.data_ptr(), _stream_ptr(stream))
+
+
+def serve_default_cfg(**overrides) -> ServeCfg:
+    c = ServeCfg()
+    _check(load().abfs_serve_default_cfg(ctypes.byref(c)), "abfs_serve_default_cfg")
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+class Server:
+    """abfs_serve_*: continuous batching of BFS queries on resident graphs."""
+
+    def __init__(self, graphs: list[Graph], cfg: ServeCfg | None = None):
+        self.graphs = list(graphs)
+        h = ctypes.c_void_p()
+        rc = load().abfs_serve_start(_ptr_array([g.handle.value for g in self.graphs]),
+                                     len(self.graphs), ctypes.byref(cfg) if cfg else None,
+                                     ctypes.byref(h))
+        _check(rc, "abfs_serve_start")
+        self.handle = h
+
+    def submit(self, graph_idx: int, source: int, level, parent) -> int | None:
+        """Queues a query into the caller's device tensors; None when the queue is full."""
+        t = ctypes.c_uint64()
+        rc = load().abfs_serve_submit(self.handle, int(graph_idx), int(source), level.data_ptr(),
+                                      parent.data_ptr(), ctypes.byref(t))
+        if rc == ERR_BUSY:
+            return None
+        _check(rc, "abfs_serve_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        done = ctypes.c_int()
+        st = ctypes.c_int32()
+        _check(load().abfs_serve_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(st)),
+               "abfs_serve_poll")
+        return bool(done.value), int(st.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> int:
+        st = ctypes.c_int32()
+        _check(load().abfs_serve_wait(self.handle, ticket, timeout_ms, ctypes.byref(st)),
+               "abfs_serve_wait")
+        return int(st.value)
+
+    def stop(self) -> dict:
+        rep = ServeReport()
+        h, self.handle = self.handle, ctypes.c_void_p(0)
+        _check(load().abfs_serve_stop(h, ctypes.byref(rep)), "abfs_serve_stop")
+        return rep.as_dict()
+
+    def __del__(self):
+        try:
+            if _lib is not None and self.handle and self.handle.value:
+                _lib.abfs_serve_stop(self.handle, None)
+        except Exception:
+            pass
 
 
 def tune(g: Graph, sources, mode: int = MODE_SUBMATRIX, cache_path: str | None = None,

@@ -152,6 +152,7 @@ EngineParams engine_params(const abfs_params& p) {
     e.shrink_theta = shrink_enabled(p) ? p.shrink_theta : 0.f;
     e.shrink_max = shrink_enabled(p) ? std::min<uint32_t>(p.shrink_max, 64) : 0;
     e.shrink_tile = kTileMax;
+    e.init_tile = 65536;
     e.timeout_ns = (unsigned long long)p.timeout_ms * 1000000ull;
     return e;
 }
@@ -394,6 +395,10 @@ int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* pa
     a.done_count = w.d_done;
     a.heartbeat = w.d_beat;
     a.prof = prof;
+    a.serve = 0;
+    a.slot_state = nullptr;
+    a.stop_flag = nullptr;
+    a.idle_exit_ns = 0;
     a.p = engine_params(p);
     CK(launch_init(a, g->n, s));
     CK(launch_engine(a, grid_size(g, p, 0), s));
@@ -411,6 +416,20 @@ int finish_stats(abfs_graph_s* g, cudaStream_t s, abfs_stats* stats) {
 }
 
 }  // namespace
+
+namespace abfs {
+int graph_arrays(abfs_graph_t g, const uint32_t** colptr, const uint32_t** rowidx, uint32_t* n,
+                 uint64_t* nnz, int* device, int* sms) {
+    if (!g) return ABFS_ERR_INVALID_ARG;
+    *colptr = g->d_colptr;
+    *rowidx = g->d_rowidx;
+    *n = g->n;
+    *nnz = g->nnz;
+    *device = g->device;
+    *sms = g->sms;
+    return ABFS_OK;
+}
+}  // namespace abfs
 
 extern "C" int abfs_default_params(abfs_params* p) {
     if (!p) return ABFS_ERR_INVALID_ARG;
@@ -687,6 +706,10 @@ extern "C" int abfs_batch_create(const abfs_graph_t* g, const uint32_t* sources,
     a.done_count = b->d_done;
     a.heartbeat = b->d_beat;
     a.prof = nullptr;
+    a.serve = 0;
+    a.slot_state = nullptr;
+    a.stop_flag = nullptr;
+    a.idle_exit_ns = 0;
     a.p = engine_params(p);
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {

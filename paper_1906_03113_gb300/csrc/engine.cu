@@ -108,6 +108,7 @@ struct Cmd {
     uint32_t nitems;
     uint32_t last;     // this CTA completed the last unit of the phase
     uint32_t quit;
+    uint32_t start;    // serving: this CTA claimed a newly submitted search
 };
 
 struct Smem {
@@ -139,6 +140,7 @@ struct Smem {
     Inst I;
     uint32_t cur_q;
     uint32_t prof_on;
+    uint32_t idle_exit;
     unsigned long long prof[kProfSlots];
 };
 
@@ -862,6 +864,26 @@ __device__ void unit_shrink(const Inst& I, InstCtl* ctl, const EngineParams& P, 
     __syncthreads();
 }
 
+// Serving: clears the outputs (and bitmaps) of vertices [u*init_tile, ...) of
+// a newly started search -- the work the initialisation kernels do for
+// abfs_run, done inside the long-lived launch.
+__device__ void unit_init(const Inst& I, const EngineParams& P, uint32_t u) {
+    const uint32_t v0 = u * P.init_tile;
+    const uint32_t v1 = min(I.n, v0 + P.init_tile);
+    for (uint32_t v = v0 + threadIdx.x; v < v1; v += kThreads) {
+        I.level[v] = -1;
+        I.parent[v] = kUnset;
+        if (P.mode == kModePlain) I.y[v] = ~0ull;
+    }
+    if (P.mode == kModeSub) {
+        const uint32_t w0 = v0 >> 5, w1 = (v1 + 31) >> 5;  // init_tile is a multiple of 32
+        for (uint32_t w = w0 + threadIdx.x; w < w1; w += kThreads) {
+            I.bm[0][w] = 0u;
+            I.bm[1][w] = 0u;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // phase control
 // ---------------------------------------------------------------------------
@@ -870,7 +892,9 @@ __device__ void unit_shrink(const Inst& I, InstCtl* ctl, const EngineParams& P, 
 template <int MODE>
 __device__ void run_unit(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                          uint32_t kind, uint32_t k, uint32_t unit, uint32_t nitems) {
-    if (kind == kPhShrink) {
+    if (kind == kPhInit) {
+        unit_init(I, P, unit);
+    } else if (kind == kPhShrink) {
         // k = level just completed; its write bitmap holds every vertex reached so far
         const uint32_t src_mat = ld_relaxed(&ctl->mat_cur);
         unit_shrink(I, ctl, P, sm, unit, I.bm[(k + 1) & 1], src_mat, /*dst=*/nitems);
@@ -901,7 +925,28 @@ template <int MODE>
 __device__ void decide_next(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                             uint32_t kind, uint32_t k, uint32_t* done_count) {
     uint32_t nkind = 0, nk = 0, ni = 0, finish = 0;
-    if (kind == kPhPlainMult) {
+    if (kind == kPhInit) {
+        // the outputs are clear: the source forms the frontier of level 0
+        // (Algorithm 1's V_2 := V_1 \ supp(x_1))
+        const uint32_t s = I.src;
+        I.level[s] = 0;
+        I.parent[s] = s;
+        if (MODE == kModeSub) atomicOr(I.bm[0] + (s >> 5), 1u << (s & 31));
+        const uint32_t b0 = ld_ro(I.colptr + s);
+        const uint32_t w = ld_ro(I.colptr + s + 1) - b0 + kVertexSlots;
+        I.fq[0][0] = s;
+        I.fbeg[0][0] = b0;
+        I.fpre[0][0] = 0;
+        I.blk[0][0].vb = 0;
+        I.blk[0][0].nv = 1;
+        I.blk[0][0].eb = 0;
+        for (unsigned long long x = 0; x < w; x += P.unit) I.ustart[0][x / P.unit] = make_uint2(0, 0);
+        st_relaxed64(&ctl->bctr[0], ((unsigned long long)w << kBlockBits) | 1ull);
+        st_relaxed(&ctl->fcnt[0], 1u);
+        st_relaxed(&ctl->reached, 1u);
+        nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
+        nk = 0;
+    } else if (kind == kPhPlainMult) {
         // comparator: the mask phase of the same level follows the multiply
         const uint32_t t = ld_relaxed(&ctl->tcnt);
         nkind = kPhPlainMask;
@@ -969,8 +1014,17 @@ __device__ void decide_next(const Inst& I, InstCtl* ctl, const EngineParams& P, 
         const uint32_t e = ld_relaxed(&ctl->err);
         __threadfence();
         if (atomicCAS(&ctl->status, (uint32_t)kRunning, e ? (uint32_t)kFailed : (uint32_t)kDone) ==
-            kRunning)
+            kRunning) {
             atomicAdd(done_count, 1u);
+            if (I.notify) {
+                // serving: the ticket and status reach the host's mapped word after
+                // every write of the search
+                __threadfence_system();
+                const unsigned long long word = (I.ticket << 8) | (unsigned long long)(e & 0xFFu);
+                asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(I.notify), "l"(word)
+                             : "memory");
+            }
+        }
     }
 }
 
@@ -1036,9 +1090,16 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
     }
 }
 
-// Whether instance q has an untaken unit in its published phase.
-__device__ __forceinline__ bool has_work(const Inst* insts, uint32_t q) {
-    InstCtl* ctl = insts[q].ctl;
+// Whether instance q has an untaken unit in its published phase (or, when
+// serving, is a newly submitted search waiting to start).
+__device__ __forceinline__ bool has_work(const EngineArgs& a, uint32_t q) {
+    if (a.serve) {
+        // a slot that never held a search has no control block yet
+        const uint32_t st = ld_relaxed(a.slot_state + q);
+        if (st == kSlotSubmitted) return true;
+        if (st != kSlotRunning) return false;
+    }
+    InstCtl* ctl = a.insts[q].ctl;
     if (ld_relaxed(&ctl->status) != kRunning) return false;
     const unsigned long long g = ld_relaxed64(&ctl->grab);
     const uint32_t e = (uint32_t)(g >> 32), taken = (uint32_t)g;
@@ -1046,9 +1107,19 @@ __device__ __forceinline__ bool has_work(const Inst* insts, uint32_t q) {
     return (uint32_t)(d >> 32) == e && taken < (uint32_t)d;
 }
 
-// One lane: takes a unit of instance q if one is left; fills sm.cmd.
-__device__ __forceinline__ bool take_unit(const Inst* insts, uint32_t q, Smem& sm) {
-    InstCtl* ctl = insts[q].ctl;
+// One lane: takes a unit of instance q if one is left (or claims the start
+// of a submitted search); fills sm.cmd.
+__device__ __forceinline__ bool take_unit(const EngineArgs& a, uint32_t q, Smem& sm) {
+    if (a.serve && ld_relaxed(a.slot_state + q) == kSlotSubmitted) {
+        if (atomicCAS(a.slot_state + q, (uint32_t)kSlotSubmitted, (uint32_t)kSlotRunning) !=
+            kSlotSubmitted)
+            return false;
+        __threadfence();  // acquire: the descriptor the host wrote before the state
+        sm.cmd.q = q;
+        sm.cmd.start = 1;
+        return true;
+    }
+    InstCtl* ctl = a.insts[q].ctl;
     const unsigned long long old = atomicAdd(&ctl->grab, 1ull);
     const uint32_t e = (uint32_t)(old >> 32), t = (uint32_t)old;
     const unsigned long long d = ld_relaxed64(&ctl->desc[e & 1]);
@@ -1056,12 +1127,37 @@ __device__ __forceinline__ bool take_unit(const Inst* insts, uint32_t q, Smem& s
     __threadfence();  // acquire: the phase fields and the data of earlier phases
     const uint32_t qq = e & 1;
     sm.cmd.q = q;
+    sm.cmd.start = 0;
     sm.cmd.epoch = e;
     sm.cmd.unit = t;
     sm.cmd.kind = ld_relaxed(&ctl->kind[qq]);
     sm.cmd.level = ld_relaxed(&ctl->plevel[qq]);
     sm.cmd.nitems = ld_relaxed(&ctl->nitems[qq]);
     return true;
+}
+
+// Serving: the CTA that claimed a submitted search resets its control block
+// and publishes the initialisation phase (epoch 0).  Whole CTA.
+__device__ void start_search(const EngineArgs& a, Smem& sm) {
+    const Inst& I = sm.I;
+    InstCtl* ctl = I.ctl;
+    uint32_t* c = reinterpret_cast<uint32_t*>(ctl);
+    for (uint32_t w = threadIdx.x; w < sizeof(InstCtl) / 4; w += kThreads) c[w] = 0u;  // status: idle
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t units = (I.n + a.p.init_tile - 1) / a.p.init_tile;
+        st_relaxed(&ctl->kind[0], kPhInit);
+        st_relaxed(&ctl->pending[0], units);
+        ctl->desc[1] = ~0ull;
+        __threadfence();
+        atomicExch(&ctl->desc[0], (unsigned long long)units);
+        atomicExch(&ctl->grab, 0ull);
+        __threadfence();
+        st_relaxed(&ctl->status, kRunning);
+        atomicAdd(a.heartbeat, 1ull);
+    }
+    __syncthreads();
 }
 
 // Warp 0 scans the instances 32 at a time from `cursor` and takes the first
@@ -1075,27 +1171,33 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
         for (uint32_t base = 0; base < a.ninst && !got; base += 32) {
             const uint32_t idx = base + lane;
             const uint32_t q = (cursor + idx) % a.ninst;
-            const bool avail = idx < a.ninst && has_work(a.insts, q);
+            const bool avail = idx < a.ninst && has_work(a, q);
             uint32_t mask = __ballot_sync(0xFFFFFFFFu, avail);
             while (mask && !got) {
                 const uint32_t l = __ffs(mask) - 1;
                 bool ok = false;
-                if (lane == l) ok = take_unit(a.insts, q, sm);
+                if (lane == l) ok = take_unit(a, q, sm);
                 got = __shfl_sync(0xFFFFFFFFu, ok, l);
                 mask &= mask - 1;
             }
         }
         __syncwarp();
-        if (lane == 0) {
-            sm.cmd.has = got;
-            if (got && sm.cur_q != sm.cmd.q) {
-                sm.I = a.insts[sm.cmd.q];
-                sm.cur_q = sm.cmd.q;
-            }
+        if (lane == 0) sm.cmd.has = got;
+        __syncwarp();
+        // serving slots are reused by new searches: always reload their descriptor
+        if (got && (a.serve || sm.cur_q != sm.cmd.q)) {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(a.insts + sm.cmd.q);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.I);
+            for (uint32_t w = lane; w < sizeof(Inst) / 4; w += 32) dst[w] = src[w];
+            if (lane == 0) sm.cur_q = sm.cmd.q;
         }
     }
     __syncthreads();
     if (!sm.cmd.has) return false;
+    if (sm.cmd.start) {
+        start_search(a, sm);
+        return true;
+    }
     prof_add(sm, kProfTake, pt0);
     if (sm.prof_on && threadIdx.x == 0) sm.prof[kProfUnits] += 1;
     cursor = sm.cmd.q;
@@ -1127,6 +1229,8 @@ __global__ void __launch_bounds__(kThreads, 2) engine_kernel(EngineArgs a) {
     if (threadIdx.x == 0) {
         for (int q = 0; q < kWarps; ++q) sm.wcnt[q] = 0;
         sm.prof_on = a.prof != nullptr;
+        sm.idle_exit = 0;
+        sm.cmd.start = 0;
         for (int q = 0; q < kProfSlots; ++q) sm.prof[q] = 0;
         sm.st_read = sm.st_unmasked = sm.st_claims = sm.st_nnz = 0;
         sm.cur_q = kUnset;
@@ -1137,7 +1241,9 @@ __global__ void __launch_bounds__(kThreads, 2) engine_kernel(EngineArgs a) {
     unsigned long long last_beat = ~0ull;
     uint32_t backoff = 64;
     for (;;) {
-        if (threadIdx.x == 0) sm.cmd.quit = (ld_relaxed(a.done_count) >= a.ninst);
+        if (threadIdx.x == 0)
+            sm.cmd.quit = a.serve ? (ld_relaxed(a.stop_flag) != 0 || sm.idle_exit)
+                                  : (ld_relaxed(a.done_count) >= a.ninst);
         __syncthreads();
         if (sm.cmd.quit) break;
         const long long pti = prof_now(sm);
@@ -1152,6 +1258,10 @@ __global__ void __launch_bounds__(kThreads, 2) engine_kernel(EngineArgs a) {
             if (beat != last_beat) {
                 last_beat = beat;
                 idle_since = now;
+            } else if (a.serve) {
+                // serving: a launch without work for idle_exit_ns ends (bounded
+                // wait); the host relaunches it when requests arrive
+                if (now - idle_since > a.idle_exit_ns) sm.idle_exit = 1;
             } else if (now - idle_since > a.p.timeout_ns) {
                 for (uint32_t q = 0; q < a.ninst; ++q) {
                     InstCtl* ctl = a.insts[q].ctl;

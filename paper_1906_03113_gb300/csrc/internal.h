@@ -43,9 +43,13 @@ enum PhaseKind : uint32_t {
     kPhPlainMult = 1,  // comparator: multiply every entry of the frontier columns
     kPhPlainMask = 2,  // comparator: apply the visited mask to the touched rows
     kPhShrink = 3,     // physical shrink of the unvisited columns
+    kPhInit = 4,       // serving: clear the outputs and bitmaps of a newly started search
 };
 
-enum InstStatus : uint32_t { kRunning = 0, kDone = 1, kFailed = 2 };
+enum InstStatus : uint32_t { kIdle = 0, kRunning = 1, kDone = 2, kFailed = 3 };
+
+// Serving slot states (device array, one word per slot).
+enum SlotState : uint32_t { kSlotFree = 0, kSlotSubmitted = 1, kSlotRunning = 2 };
 
 // A block of the frontier: nv consecutive vertices at fq[vb..], whose column
 // entries occupy [eb, eb + sum of their weights) of the level's entry space.
@@ -114,7 +118,9 @@ struct Inst {
     InstCtl* ctl;
     uint4* trace;            // optional per-phase trace (nullptr = off)
     uint32_t trace_cap;
-    uint32_t pad_;
+    uint32_t slot;           // serving: slot index
+    unsigned long long ticket;       // serving: request ticket
+    unsigned long long* notify;      // serving: host-mapped word that receives ticket<<8 | status
 };
 
 struct EngineParams {
@@ -126,6 +132,7 @@ struct EngineParams {
     float shrink_theta;
     uint32_t shrink_max;
     uint32_t shrink_tile;          // vertices per shrink unit
+    uint32_t init_tile;            // serving: vertices per initialisation unit
     unsigned long long timeout_ns;
 };
 
@@ -135,6 +142,10 @@ struct EngineArgs {
     uint32_t* done_count;          // instances finished (any status)
     unsigned long long* heartbeat; // progress counter for the bounded waits
     unsigned long long* prof;      // optional per-category CTA cycle totals (kProfSlots), or null
+    uint32_t serve;                // 1: long-lived serving launch over a slot table
+    uint32_t* slot_state;          // serving: SlotState per slot
+    const uint32_t* stop_flag;     // serving: host sets 1 to end the launch
+    unsigned long long idle_exit_ns;  // serving: the launch ends after this long without progress
     EngineParams p;
 };
 
@@ -169,6 +180,8 @@ Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p);
 Inst make_inst_raw(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, char* base,
                    const Layout& L, uint32_t src, int32_t* level, int32_t* parent);
 int grid_for(int sms, const abfs_params& p);
+int graph_arrays(abfs_graph_t g, const uint32_t** colptr, const uint32_t** rowidx, uint32_t* n,
+                 uint64_t* nnz, int* device, int* sms);
 
 // Launch helpers implemented in engine.cu.
 cudaError_t launch_put_inst(const Inst& inst, Inst* dst, cudaStream_t s);

@@ -82,6 +82,10 @@ extern "C" int abfs_run_static(const uint32_t* colptr, const uint32_t* rowidx, u
     a.done_count = static_cast<uint32_t*>(ws);
     a.heartbeat = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + 8);
     a.prof = nullptr;
+    a.serve = 0;
+    a.slot_state = nullptr;
+    a.stop_flag = nullptr;
+    a.idle_exit_ns = 0;
     a.p = engine_params(p);
     // the initialisation kernels clear every word a search expects at zero
     // (bitmaps, control block, counters); the rest is written before it is read

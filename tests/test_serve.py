@@ -1,0 +1,112 @@
+"""Serving (continuous batching): every result equals the same query run alone.
+
+Queries arrive in bursts while others are on the device; a small memory
+budget forces memory-gated admission.  The bar is bit-exact equality with
+abfs_run (itself equal to the oracle)."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+
+import paper_1906_03113_gb300 as abfs  # noqa: E402
+from paper_1906_03113_gb300 import binding  # noqa: E402
+
+
+def test_default_cfg_and_argument_checks():
+    abfs.build()
+    c = abfs.serve_default_cfg()
+    assert c.max_slots >= 1 and c.queue_capacity >= 1 and c.memory_budget > 0
+    assert c.idle_exit_ms >= 1 and c.params.unit_entries >= 256
+    lib = abfs.load()
+    import ctypes
+    out = ctypes.c_void_p()
+    assert lib.abfs_serve_start(None, 0, None, ctypes.byref(out)) == binding.ERR_INVALID_ARG
+    assert lib.abfs_serve_stop(None, None) == binding.ERR_INVALID_ARG
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    abfs.build()
+    abfs.load()
+    torch.cuda.set_device(0)
+    gs = [synth.er_2_16(), synth.rmat(14, 16.0, seed=3), synth.grid(100, 37),
+          synth.rgg_knn(1 << 15, 4, seed=4), synth.rmat(16, 8.0, seed=9)]
+    dev = [abfs.graph_create(g.colptr, g.rowidx, directed=g.directed) for g in gs]
+    yield gs, dev
+    for G in dev:
+        G.destroy()
+
+
+def _queries(gs, count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        gi = int(rng.integers(len(gs)))
+        deg = gs[gi].degrees()
+        cand = np.nonzero(deg > 0)[0]
+        out.append((gi, int(cand[rng.integers(cand.size)])))
+    return out
+
+
+def _serve_and_check(gs, dev, queries, cfg, bursts):
+    srv = abfs.Server(dev, cfg)
+    outs = []
+    tickets = []
+    per = (len(queries) + bursts - 1) // bursts
+    for b in range(bursts):
+        for gi, s in queries[b * per:(b + 1) * per]:
+            lev = torch.empty(gs[gi].n, dtype=torch.int32, device="cuda")
+            par = torch.empty(gs[gi].n, dtype=torch.int32, device="cuda")
+            t = srv.submit(gi, s, lev, par)
+            assert t is not None
+            tickets.append(t)
+            outs.append((gi, s, lev, par))
+        if b == 0:
+            # later bursts arrive while the first ones are on the device
+            srv.poll(tickets[0])
+    for t in tickets:
+        assert srv.wait(t, 60000) == 0
+    rep = srv.stop()
+    assert rep["completed"] == len(queries) == rep["submitted"] and rep["failed"] == 0
+    assert rep["launches"] >= 1 and 0 < rep["p50_ms"] <= rep["p99_ms"] <= rep["max_ms"]
+    torch.cuda.synchronize()
+    for gi, s, lev, par in outs:
+        la, pa = abfs.run(dev[gi], s)
+        assert torch.equal(la, lev) and torch.equal(pa, par), (gi, s)
+    return rep
+
+
+@pytest.mark.gpu
+def test_serve_mix_equals_alone(graphs):
+    gs, dev = graphs
+    cfg = abfs.serve_default_cfg(max_slots=32, memory_budget=2 << 30, idle_exit_ms=20)
+    _serve_and_check(gs, dev, _queries(gs, 300, 1), cfg, bursts=6)
+
+
+@pytest.mark.gpu
+def test_serve_memory_gated_admission(graphs):
+    gs, dev = graphs
+    # a budget that holds only one or two queries of the largest graph at a time
+    big = max(G.footprint() for G in dev)
+    cfg = abfs.serve_default_cfg(max_slots=64, memory_budget=int(big * 2.2), idle_exit_ms=5)
+    _serve_and_check(gs, dev, _queries(gs, 80, 2), cfg, bursts=3)
+
+
+@pytest.mark.gpu
+def test_serve_queue_full_is_busy(graphs):
+    gs, dev = graphs
+    cfg = abfs.serve_default_cfg(max_slots=1, queue_capacity=2, memory_budget=1 << 30)
+    srv = abfs.Server(dev, cfg)
+    bufs = [(torch.empty(gs[0].n, dtype=torch.int32, device="cuda"),
+             torch.empty(gs[0].n, dtype=torch.int32, device="cuda")) for _ in range(64)]
+    results = [srv.submit(0, 0, lv, pr) for lv, pr in bufs]
+    assert any(r is None for r in results)          # some were refused: queue full
+    for t in results:
+        if t is not None:
+            assert srv.wait(t, 60000) == 0
+    rep = srv.stop()
+    assert rep["completed"] == sum(r is not None for r in results)
