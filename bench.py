@@ -190,6 +190,163 @@ def cpu_baseline(g, srcs, max_seconds=20.0):
                       f"({total:.1f} s)"}
 
 
+def _edges(st, directed):
+    return st["nnz_reached"] if directed else st["nnz_reached"] / 2.0
+
+
+def bench_batch(args, ws, rank, local, torch, abfs, dist):
+    """512 ER/R-MAT graphs (n log-uniform in [2^10, 2^18], average degree U[4, 32])
+    plus 64 sources on R-MAT-22, all in one persistent launch replayed from a
+    CUDA graph, against the same queries as single-query launches."""
+    specs = synth.batch_specs(512, seed=1)
+    hosts = [synth.make_batch_graph(sp) for sp in specs]
+    big = synth.rmat_22()
+    graphs = [abfs.graph_create(h.colptr, h.rowidx, directed=False) for h in hosts]
+    G22 = abfs.graph_create(big.colptr, big.rowidx, directed=False)
+    srcs = [int(synth.sources_with_degree(h, 1, seed=1 + i)[0]) if (h.degrees() > 0).any() else 0
+            for i, h in enumerate(hosts)]
+    src22 = [int(x) for x in synth.sources_with_degree(big, 64, seed=2)]
+    qg = graphs + [G22] * 64
+    qs = srcs + src22
+    qd = [h.directed for h in hosts] + [False] * 64
+    stream = torch.cuda.current_stream()
+    # edges of each query's component (from a counting run, outside the timing)
+    edges = []
+    lv = torch.empty(big.n, dtype=torch.int32, device="cuda")
+    pv = torch.empty(big.n, dtype=torch.int32, device="cuda")
+    for G, s_, d in zip(qg, qs, qd):
+        _, _, st = abfs.run(G, s_, lv[:G.n], pv[:G.n], stream, None, stats=True)
+        edges.append(_edges(st, d))
+    total_edges = float(sum(edges))
+    plan = abfs.BatchPlan(qg, qs)
+    for _ in range(max(args.warmup, 3)):
+        plan.launch(stream)
+    torch.cuda.synchronize()
+    assert all(x == 0 for x in plan.status()), "batch failed"
+    steps = max(1, min(args.steps, 20))
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    a.record(stream)
+    for _ in range(steps):
+        plan.launch(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    batch_ms = a.elapsed_time(b) / steps
+    # the same queries, one launch each
+    a.record(stream)
+    for G, s_ in zip(qg, qs):
+        abfs.run(G, s_, lv[:G.n], pv[:G.n], stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    single_ms = a.elapsed_time(b)
+    nq = len(qg)
+    value = total_edges / (batch_ms * 1e-3) / 1e9
+    line = {
+        "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": batch_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "batch512_rmat22x64",
+                   "graph": "512 ER/R-MAT graphs, n log-uniform in [2^10, 2^18], avg degree "
+                            "U[4,32] (seed 1), plus 64 sources on R-MAT-22 (seed 2)",
+                   "queries": nq, "step": "one persistent launch (CUDA graph replay) of all queries",
+                   "l2": "inputs larger than L2 (R-MAT-22 rowidx 513 MB, 576 workspaces)"},
+        "batched": {"ms": batch_ms, "queries_per_s": nq / (batch_ms * 1e-3), "gteps": value,
+                    "single_query_ms": single_ms,
+                    "single_query_gteps": total_edges / (single_ms * 1e-3) / 1e9,
+                    "speedup_vs_single": single_ms / batch_ms},
+        "gpu_launches": 3 * steps, "clocks": clk,
+    }
+    plan.destroy()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def bench_serve(args, ws, rank, local, torch, abfs, dist):
+    """32 resident graphs (16 R-MAT of scales 16..22, 15 ER of 2^16..2^20
+    vertices, one 2048 x 2048 grid); queries with a uniform graph and source
+    (degree >= 1) arrive as a Poisson stream at 0.5, 0.8 and 1.0 x the
+    saturation rate measured first with a closed burst."""
+    specs = synth.serve_graph_specs()
+    hosts = [synth.make_serve_graph(k, kw) for k, kw in specs]
+    graphs = [abfs.graph_create(h.colptr, h.rowidx, directed=False) for h in hosts]
+    cand = [np.nonzero(h.degrees() > 0)[0].astype(np.int64) for h in hosts]
+    rng = np.random.default_rng(1)
+    nq = max(1000, args.queries)
+    qg = rng.integers(len(hosts), size=nq)
+    qs = np.array([cand[g][rng.integers(cand[g].size)] for g in qg], dtype=np.int64)
+    pool = 48  # output buffers per graph
+    bufs = [[(torch.empty(h.n, dtype=torch.int32, device="cuda"),
+              torch.empty(h.n, dtype=torch.int32, device="cuda")) for _ in range(pool)]
+            for h in hosts]
+    cfg = abfs.serve_default_cfg(max_slots=256, memory_budget=48 << 30, idle_exit_ms=50)
+
+    def run(rate, count):
+        srv = abfs.Server(graphs, cfg)
+        free = [list(range(pool)) for _ in hosts]
+        outstanding = {}   # ticket -> (graph, buffer)
+        waits = 0
+        t0 = time.perf_counter()
+        gap = np.random.default_rng(7).exponential(1.0 / rate, size=count) if rate else None
+        t_next = t0
+        for i in range(count):
+            if rate:
+                t_next += gap[i]
+                while time.perf_counter() < t_next:
+                    pass
+            g = int(qg[i % nq])
+            while not free[g]:
+                waits += 1
+                for t, (gg, bi) in list(outstanding.items()):
+                    done, _ = srv.poll(t)
+                    if done:
+                        free[gg].append(bi)
+                        del outstanding[t]
+            bi = free[g].pop()
+            lv, pv = bufs[g][bi]
+            while True:
+                t = srv.submit(g, int(qs[i % nq]), lv, pv)
+                if t is not None:
+                    break
+            outstanding[t] = (g, bi)
+            if len(outstanding) > 512 and i % 64 == 0:
+                for t2, (gg, b2) in list(outstanding.items()):
+                    done, _ = srv.poll(t2)
+                    if done:
+                        free[gg].append(b2)
+                        del outstanding[t2]
+        for t in list(outstanding):
+            srv.wait(t, 600000)
+        rep = srv.stop()
+        rep["offered_qps"] = rate
+        rep["buffer_waits"] = waits
+        return rep
+
+    sat = run(0.0, min(nq, 20000))              # closed burst: saturation throughput
+    rates = [0.5, 0.8, 1.0]
+    per = [run(f * sat["qps"], nq) for f in rates]
+    best = per[-1]
+    line = {
+        "metric": "queries/s", "value": best["qps"], "unit": "queries/s", "n_gpus": ws,
+        "steps": len(rates), "warmup": 1, "ms_per_step": best["wall_s"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "serve32_poisson",
+                   "graph": "32 resident graphs: 16 R-MAT (scales 16..22), 15 ER (2^16..2^20, d=8), "
+                            "one 2048x2048 grid",
+                   "queries_per_rate": nq, "arrivals": "Poisson at 0.5/0.8/1.0 x saturation"},
+        "saturation": {k: sat[k] for k in ("qps", "p50_ms", "p99_ms", "completed", "launches")},
+        "rates": [{k: r[k] for k in ("offered_qps", "qps", "p50_ms", "p99_ms", "mean_ms", "max_ms",
+                                     "completed", "launches", "buffer_waits")} for r in per],
+        "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,7 +354,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22",
-                    choices=["rmat22", "er16", "grid4096", "rgg22"])
+                    choices=["rmat22", "er16", "grid4096", "rgg22", "batch512", "serve"])
+    ap.add_argument("--queries", type=int, default=100000, help="serve: queries per arrival rate")
     ap.add_argument("--mode", default="sub", choices=["sub", "plain"])
     ap.add_argument("--shrink", type=float, default=0.0)
     ap.add_argument("--no-extras", action="store_true")
@@ -218,6 +376,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     abfs.load()
+    if args.workload == "batch512":
+        return bench_batch(args, ws, rank, local, torch, abfs, dist)
+    if args.workload == "serve":
+        return bench_serve(args, ws, rank, local, torch, abfs, dist)
 
     g, srcs, (wname, wdesc) = make_workload(args.workload)
     G = abfs.graph_create(g.colptr, g.rowidx, directed=g.directed)
