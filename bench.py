@@ -47,6 +47,35 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def _engine_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("engine.cu", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1906_03113_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _profiled_traffic(workload: str):
+    """DRAM bytes per engine launch from the committed ncu summary of this
+    workload, or None when the engine source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"engine_kernel_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as fh:
+        for ln in fh:
+            m = ln.strip().split(":", 1)
+            if len(m) == 2 and m[0] in ("traffic_bytes_per_launch", "engine_source_sha256"):
+                fields[m[0]] = m[1].strip()
+    if fields.get("engine_source_sha256") != _engine_sha256():
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -469,7 +498,8 @@ def main():
                    "parallelism": f"replicas x{ws}", "edges": "m_c = nnz_c/2" if not g.directed
                    else "m_c = nnz_c"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                     "frac": achieved / hbm, "peak_kind": peak_kind,
+                     "traffic": _profiled_traffic(wname),
                      "kernel": "engine_kernel<0> (one launch per BFS, with 3 small init kernels)",
                      "bytes_per_bfs": float(b_alg.mean()),
                      "bytes_formula": "4*E_adj + 24*n_c",
