@@ -76,7 +76,9 @@ typedef enum {
 typedef struct {
     uint32_t mode;            /* ABFS_MODE_SUBMATRIX or ABFS_MODE_PLAIN */
     uint32_t tile;            /* frontier vertices staged per step, 32..1024, multiple of 32 */
-    uint32_t unit_entries;    /* entry slots per work unit, 256..16384, multiple of 256 */
+    uint32_t unit_entries;    /* granule of work units in entry slots, 256..16384, multiple of
+                                 256; a level's units are 1..16384/unit_entries granules, chosen
+                                 per level for about two units per CTA of the grid */
     uint32_t narrow_max;      /* frontiers of <= this many vertices ... */
     uint32_t narrow_edges;    /* ... and <= this many column entries run on one CTA */
     uint32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x SM count (capped by occupancy) */
@@ -84,6 +86,13 @@ typedef struct {
                                  <= 0 or >= 1 disables it */
     uint32_t shrink_max;      /* at most this many shrinks per search */
     uint32_t timeout_ms;      /* bound on any device-side wait without progress */
+    uint32_t narrow_resident; /* 1: consecutive narrow levels run back to back on one CTA with
+                                 the frontier kept as a plain list (no per-level hand-off);
+                                 0: every narrow level goes through the block bookkeeping */
+    uint32_t claim_scan;      /* submatrix mode: a wide level with at least this many entry
+                                 slots multiplies and claims by reductions (no returned
+                                 values), and a scan of the visited bitmaps then collects the
+                                 vertices it reached; 0: never */
 } abfs_params;
 
 /* Per-search counters, filled when a stats pointer is passed. */
@@ -161,9 +170,13 @@ int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_host, int32_t*
  * receives up to `cap` entries of 8 uint32 each --
  *   [0..1] %globaltimer (ns, low/high), [2] phase kind << 24 | BFS level
  *   (kind 0 level, 1 comparator multiply, 2 comparator mask, 3 shrink,
- *   0xFE start, 0xFF end), [3] 1 if the phase ran on one CTA,
- *   [4] heavy-chunk units, [5] frontier vertices (or touched rows),
- *   [6] column entries of that frontier, [7] 0.
+ *   5 level claimed by reductions, 6 extraction of its new vertices,
+ *   0xFE start, 0xFF end), [3] 0 if the phase was published to the whole
+ *   grid, 1 if it ran on one CTA, 2 if it is a further level of a resident
+ *   narrow run, [4] units or touched rows of the phase, [5] frontier
+ *   vertices, [6] entry slots of that frontier (column entries + 2 per
+ *   vertex, low 32 bits), [7] 0.  For a level, [4] is its number of work
+ *   units (comparator mask: touched rows).
  * *count receives the number written.  Synchronises `stream`.
  */
 int abfs_run_trace(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,

@@ -45,6 +45,8 @@ class Params(ctypes.Structure):
         ("shrink_theta", ctypes.c_float),
         ("shrink_max", ctypes.c_uint32),
         ("timeout_ms", ctypes.c_uint32),
+        ("narrow_resident", ctypes.c_uint32),
+        ("claim_scan", ctypes.c_uint32),
     ]
 
     def as_dict(self) -> dict:
@@ -281,8 +283,8 @@ def run(g: Graph, source: int, level=None, parent=None, stream=None, params: Par
     return (level, parent, st.as_dict()) if stats else (level, parent)
 
 
-TRACE_KINDS = {0: "level", 1: "plain_mult", 2: "plain_mask", 3: "shrink", 0xFE: "start",
-               0xFF: "end"}
+TRACE_KINDS = {0: "level", 1: "plain_mult", 2: "plain_mask", 3: "shrink", 4: "init",
+               5: "level_scan", 6: "extract", 0xFE: "start", 0xFF: "end"}
 
 
 def run_trace(g: Graph, source: int, params: Params | None = None, cap: int = 4096, stream=None):
@@ -300,9 +302,11 @@ def run_trace(g: Graph, source: int, params: Params | None = None, cap: int = 40
     t0 = None
     prof_at = [i for i, r in enumerate(rows) if (int(r[2]) >> 24) == 0xFD]
     if prof_at:
-        flat = rows[prof_at[0]:prof_at[0] + 3].reshape(-1)[4:]
-        vals = [int(flat[2 * q] | (flat[2 * q + 1] << 32)) for q in range(8)]
-        names = ["idle", "take", "gather", "expand", "wait", "flush", "advance", "units"]
+        flat = rows[prof_at[0]:].reshape(-1)[4:]
+        names = ["idle", "take", "gather", "expand", "wait", "flush", "advance", "units",
+                 "narrow_load", "narrow_expand", "narrow_append", "narrow_decide", "narrow_blocks",
+                 "narrow_levels", "x_setup", "x_loop", "x_process", "x_flush", "x_calls"]
+        vals = [int(flat[2 * q] | (flat[2 * q + 1] << 32)) for q in range(len(names))]
         out_prof = dict(zip(names, vals))
         rows = rows[:prof_at[0]]
     else:

@@ -41,7 +41,7 @@ extern "C" const char* abfs_strerror(int status) {
     }
 }
 
-extern "C" int abfs_version(void) { return 10000; }
+extern "C" int abfs_version(void) { return 10100; }
 
 namespace {
 
@@ -116,13 +116,15 @@ abfs_params default_params() {
     abfs_params p;
     p.mode = ABFS_MODE_SUBMATRIX;
     p.tile = 1024;
-    p.unit_entries = 16384;
+    p.unit_entries = 1024;
     p.narrow_max = 1024;
     p.narrow_edges = 16384;
     p.ctas_per_sm = 2;
     p.shrink_theta = 0.f;
     p.shrink_max = 0;
     p.timeout_ms = 10000;
+    p.narrow_resident = 1;
+    p.claim_scan = 1u << 22;
     return p;
 }
 
@@ -139,6 +141,7 @@ int check_params(const abfs_params& p) {
     if (p.ctas_per_sm < 1 || p.ctas_per_sm > 8) return ABFS_ERR_INVALID_ARG;
     if (!(p.shrink_theta >= 0.f) || p.shrink_theta > 1.f) return ABFS_ERR_INVALID_ARG;
     if (p.timeout_ms < 1 || p.timeout_ms > 600000) return ABFS_ERR_INVALID_ARG;
+    if (p.narrow_resident > 1) return ABFS_ERR_INVALID_ARG;
     return ABFS_OK;
 }
 
@@ -149,6 +152,8 @@ EngineParams engine_params(const abfs_params& p) {
     e.unit = p.unit_entries;
     e.narrow_max = p.narrow_max;
     e.narrow_edges = p.narrow_edges;
+    e.narrow_loop = p.narrow_resident;
+    e.scan_min = p.mode == ABFS_MODE_SUBMATRIX ? p.claim_scan : 0u;
     e.shrink_theta = shrink_enabled(p) ? p.shrink_theta : 0.f;
     e.shrink_max = shrink_enabled(p) ? std::min<uint32_t>(p.shrink_max, 64) : 0;
     e.shrink_tile = kTileMax;
@@ -573,9 +578,10 @@ extern "C" int abfs_run_trace(abfs_graph_t g, uint32_t source, int32_t* level, i
         dev_free(d_trace);
         return ABFS_ERR_CUDA;
     }
-    // the last three entries carry the CTA cycle accounting (kind 0xFD):
+    // the last kProfEntries entries carry the CTA cycle accounting (kind 0xFD):
     // a header of 4 words, then kProfSlots 64-bit totals
-    const uint32_t tcap = cap > 3 ? cap - 3 : 0;
+    constexpr uint32_t kProfEntries = (4 + 2 * kProfSlots + 7) / 8;
+    const uint32_t tcap = cap > kProfEntries ? cap - kProfEntries : 0;
     rc = enqueue_single(g, source, level, parent, s, p, d_trace, tcap, d_prof);
     if (!rc) {
         abfs_stats st;
@@ -588,7 +594,7 @@ extern "C" int abfs_run_trace(abfs_graph_t g, uint32_t source, int32_t* level, i
         if (cudaMemcpy(prof, d_prof, sizeof(prof), cudaMemcpyDeviceToHost) != cudaSuccess)
             rc = ABFS_ERR_CUDA;
         uint32_t* out = trace_host + (size_t)n * 8;
-        if (cap <= 3) out = nullptr;
+        if (cap <= kProfEntries) out = nullptr;
         if (out) {
         out[0] = 0;
         out[1] = 0;
@@ -598,9 +604,9 @@ extern "C" int abfs_run_trace(abfs_graph_t g, uint32_t source, int32_t* level, i
             out[4 + 2 * q] = (uint32_t)prof[q];
             out[5 + 2 * q] = (uint32_t)(prof[q] >> 32);
         }
-        for (int q = 4 + 2 * kProfSlots; q < 24; ++q) out[q] = 0;
+        for (uint32_t q = 4 + 2 * kProfSlots; q < 8 * kProfEntries; ++q) out[q] = 0;
         }
-        *count = (cap > 3) ? n + 3 : n;
+        *count = (cap > kProfEntries) ? n + kProfEntries : n;
         // the workspace descriptor keeps no pointer to the freed trace buffer
         launch_set_query(g->ws.d_inst, 0, nullptr, nullptr, nullptr, 0, s);
         cudaStreamSynchronize(s);
@@ -795,7 +801,8 @@ std::string params_json(const abfs_params& p) {
       << ",\"narrow_max\":" << p.narrow_max
       << ",\"narrow_edges\":" << p.narrow_edges
       << ",\"ctas_per_sm\":" << p.ctas_per_sm << ",\"shrink_theta\":" << p.shrink_theta
-      << ",\"shrink_max\":" << p.shrink_max;
+      << ",\"shrink_max\":" << p.shrink_max << ",\"narrow_resident\":" << p.narrow_resident
+      << ",\"claim_scan\":" << p.claim_scan;
     return o.str();
 }
 
@@ -850,6 +857,8 @@ extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count
             if (json_num(found, "ctas_per_sm", &v)) p.ctas_per_sm = (uint32_t)v;
             if (json_num(found, "shrink_theta", &v)) p.shrink_theta = (float)v;
             if (json_num(found, "shrink_max", &v)) p.shrink_max = (uint32_t)v;
+            if (json_num(found, "narrow_resident", &v)) p.narrow_resident = (uint32_t)v;
+            if (json_num(found, "claim_scan", &v)) p.claim_scan = (uint32_t)v;
             p.mode = mode;
             if (check_params(p) == ABFS_OK) {
                 std::lock_guard<std::mutex> lk(g->mu);
@@ -863,8 +872,8 @@ extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count
     }
     // candidate sets
     std::vector<abfs_params> cands;
-    const uint32_t units[] = {4096, 8192, 16384};
-    const uint32_t narrow_e[] = {0, 4096, 32768};
+    const uint32_t units[] = {512, 1024, 4096};
+    const uint32_t narrow_e[] = {0, 16384, 65536};
     const uint32_t ctas[] = {1, 2};
     for (uint32_t ue : units)
         for (uint32_t ne : narrow_e)
@@ -873,7 +882,7 @@ extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count
                 p.mode = mode;
                 p.unit_entries = ue;
                 p.narrow_edges = ne;
-                p.narrow_max = ne ? 2048 : 0;
+                p.narrow_max = ne ? ne / 8 : 0;
                 p.ctas_per_sm = cp;
                 cands.push_back(p);
             }

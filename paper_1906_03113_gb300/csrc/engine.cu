@@ -46,11 +46,27 @@
 // progress.  On expiry the CTA marks the searches failed (ABFS_ERR_TIMEOUT) and
 // returns.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "internal.h"
 
 namespace abfs {
+
+// The phases and the expand loop are separate functions: each gets its own
+// register allocation, so the cold paths' state does not push the hot loop
+// into spills.  -DABFS_INLINE_ALL inlines them instead.
+// Longest sleep of an idle CTA between polls for work.
+#ifndef ABFS_IDLE_BACKOFF_NS
+#define ABFS_IDLE_BACKOFF_NS 2048
+#endif
+constexpr uint32_t kIdleBackoffMaxNs = ABFS_IDLE_BACKOFF_NS;
+
+#ifdef ABFS_INLINE_ALL
+#define ABFS_NOINLINE
+#else
+#define ABFS_NOINLINE __noinline__
+#endif
 
 // ---------------------------------------------------------------------------
 // memory-ordering helpers
@@ -136,6 +152,9 @@ struct Smem {
     uint32_t seg_idx[32], seg_pos[32];
     unsigned long long seg_eb[32];
     unsigned long long st_read, st_unmasked, st_claims, st_nnz;
+    // resident narrow run: list counters and the search's state between levels
+    uint32_t nq_cnt, nt_cnt, nr_f, nr_reached, nr_shrinks, nr_stop, nr_sw, nr_mcur, nr_mprev;
+    unsigned long long nq_slots;
     Cmd cmd;
     Inst I;
     uint32_t cur_q;
@@ -200,7 +219,7 @@ __device__ void block_exclusive_scan(uint32_t* a, uint32_t cnt, Smem& sm) {
     if (tid == 0) a[cnt] = sm.warp_sums[kWarps];
     __syncthreads();
 }
-constexpr int kTileItems = kTileMax / kThreads;
+constexpr int kTileItems = (kTileMax + kThreads - 1) / kThreads;
 
 // Column of vertex v in matrix `mat` (0 = input, 1/2 = shrunk copies).
 struct ColRef {
@@ -231,6 +250,16 @@ __device__ __forceinline__ uint32_t mat_for_level(const InstCtl* ctl, uint32_t l
     // the start of a unit orders these reads.
     const uint32_t sw = ld_relaxed(&ctl->mat_switch);
     return lvl >= sw ? ld_relaxed(&ctl->mat_cur) : ld_relaxed(&ctl->mat_prev);
+}
+
+// Matrices read by levels k and k+1, from one round of independent loads.
+__device__ __forceinline__ void level_mats(const InstCtl* ctl, uint32_t k, uint32_t& mat,
+                                           uint32_t& mat_next) {
+    const uint32_t sw = ld_relaxed(&ctl->mat_switch);
+    const uint32_t cur = ld_relaxed(&ctl->mat_cur);
+    const uint32_t prev = ld_relaxed(&ctl->mat_prev);
+    mat = k >= sw ? cur : prev;
+    mat_next = k + 1 >= sw ? cur : prev;
 }
 
 __device__ __forceinline__ void fail(InstCtl* ctl, uint32_t code) { atomicCAS(&ctl->err, 0u, code); }
@@ -264,16 +293,40 @@ __device__ __forceinline__ uint32_t ld_row(const uint32_t* rows, uint32_t idx, u
 // appending newly reached vertices as frontier blocks
 // ---------------------------------------------------------------------------
 
-// Vertex i of block blk (entry range [g0, g0 + w)) owns the unit starts that
-// fall inside its range.
-__device__ __forceinline__ void write_unit_starts(const Inst& I, InstCtl* ctl, const EngineParams& P,
-                                                  uint32_t pn, uint32_t blk, uint32_t i,
-                                                  unsigned long long g0, uint32_t w) {
+// Each lane's vertex i of block blk (entry range [g0, g0 + w); w = 0: no
+// vertex) owns the unit starts (multiples of P.unit) inside its range; the
+// warp writes them together, 32 starts per round, so one long column does not
+// serialise its lane.  Whole warp.
+__device__ __forceinline__ void warp_unit_starts(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                                 uint32_t pn, uint32_t blk, uint32_t i,
+                                                 unsigned long long g0, uint32_t w) {
+    const uint32_t lane = threadIdx.x & 31;
     const unsigned long long U = P.unit;
-    for (unsigned long long x = (g0 + U - 1) / U * U; x < g0 + w; x += U) {
-        const unsigned long long u = x / U;
-        if (u < I.ucap) I.ustart[pn][u] = make_uint2(blk, i);
-        else fail(ctl, 7 /* ABFS_ERR_DEVICE */);
+    unsigned long long uf = 0;
+    uint32_t c = 0;
+    if (w) {
+        uf = (g0 + U - 1) / U;
+        c = (uint32_t)((g0 + w + U - 1) / U - uf);
+    }
+    const uint32_t incl = warp_incl_scan(c);
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        // owner: the first lane whose inclusive count exceeds t
+        uint32_t owner = 0;
+#pragma unroll
+        for (uint32_t d = 16; d > 0; d >>= 1) {
+            const uint32_t probe = __shfl_sync(0xFFFFFFFFu, incl, owner + d - 1);
+            if (t >= probe) owner += d;
+        }
+        const unsigned long long o_uf = __shfl_sync(0xFFFFFFFFu, uf, owner);
+        const uint32_t o_excl = __shfl_sync(0xFFFFFFFFu, incl - c, owner);
+        const uint32_t o_i = __shfl_sync(0xFFFFFFFFu, i, owner);
+        if (t < total) {
+            const unsigned long long u = o_uf + (t - o_excl);
+            if (u < I.ucap) I.ustart[pn][u] = make_uint2(blk, o_i);
+            else fail(ctl, 7 /* ABFS_ERR_DEVICE */);
+        }
     }
 }
 
@@ -347,21 +400,21 @@ __device__ __forceinline__ void warp_emit(Smem& sm, const Inst& I, InstCtl* ctl,
         }
         const uint32_t w = i < n ? c.len + kVertexSlots : 0u;
         const uint32_t incl = warp_incl_scan(w);
+        const uint32_t pre = carry + incl - w;
         if (i < n) {
             const uint32_t at = vb + voff + i;
-            const uint32_t pre = carry + incl - w;
             I.fq[pn][at] = v;
             I.fbeg[pn][at] = c.beg;
             I.fpre[pn][at] = pre;
-            write_unit_starts(I, ctl, P, pn, blk, voff + i, eb + pre, w);
         }
+        warp_unit_starts(I, ctl, P, pn, blk, voff + i, eb + pre, w);
         carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
     }
     __syncwarp();
 }
 
 // A warp writes its staging buffer out as a frontier block of its own.
-__device__ void warp_flush(Smem& sm, const Inst& I, InstCtl* ctl, const EngineParams& P,
+__device__ ABFS_NOINLINE void warp_flush(Smem& sm, const Inst& I, InstCtl* ctl, const EngineParams& P,
                            uint32_t pn, uint32_t mat_next, uint32_t& wc) {
     const uint32_t n = wc;
     const uint32_t wtot = warp_weight(sm, I, mat_next, n);
@@ -378,7 +431,7 @@ __device__ void warp_flush(Smem& sm, const Inst& I, InstCtl* ctl, const EnginePa
 
 // End of a unit: the leftovers of all warps (counts in sm.wcnt) leave as one
 // frontier block.  Whole CTA.
-__device__ void cta_flush(Smem& sm, const Inst& I, InstCtl* ctl, const EngineParams& P,
+__device__ ABFS_NOINLINE void cta_flush(Smem& sm, const Inst& I, InstCtl* ctl, const EngineParams& P,
                           uint32_t pn, uint32_t mat_next) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
@@ -415,6 +468,73 @@ __device__ void cta_flush(Smem& sm, const Inst& I, InstCtl* ctl, const EnginePar
     __syncthreads();
 }
 
+// Resident narrow runs: a warp appends its n staged vertices to the frontier
+// list of parity pn (vertex, column begin, column length in matrix mat_next),
+// at a position taken from a shared-memory counter.  Whole warp.
+__device__ __forceinline__ void narrow_append(Smem& sm, const Inst& I, InstCtl* ctl, uint32_t pn, uint32_t mat_next,
+                              uint32_t& wc) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t n = wc;
+    const uint32_t* wv = sm.wv[threadIdx.x >> 5];
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&sm.nq_cnt, n);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    uint32_t wsum = 0;
+    for (uint32_t i0 = 0; i0 < n; i0 += 32 * kIlp) {
+        uint32_t v[kIlp];
+        ColRef c[kIlp];
+#pragma unroll
+        for (int q = 0; q < kIlp; ++q) {
+            const uint32_t i = i0 + 32 * q + lane;
+            v[q] = 0;
+            c[q].beg = 0;
+            c[q].len = 0;
+            if (i < n) {
+                v[q] = wv[i];
+                c[q] = col_of(I, mat_next, v[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kIlp; ++q) {
+            const uint32_t i = i0 + 32 * q + lane;
+            if (i < n) {
+                const uint32_t at = base + i;
+                if (at < I.n) {
+                    I.fq[pn][at] = v[q];
+                    I.fbeg[pn][at] = c[q].beg;
+                    I.fpre[pn][at] = c[q].len;
+                } else {
+                    fail(ctl, 7);
+                }
+                wsum += c[q].len + kVertexSlots;
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) wsum += __shfl_xor_sync(0xFFFFFFFFu, wsum, d);
+    if (lane == 0 && n) atomicAdd(&sm.nq_slots, (unsigned long long)wsum);
+    __syncwarp();
+    wc = 0;
+}
+
+// Resident narrow runs of the comparator: a warp appends its n staged
+// first-touched rows to the touched list.  Whole warp.
+__device__ __forceinline__ void narrow_touch(Smem& sm, const Inst& I, InstCtl* ctl, uint32_t& wc) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t n = wc;
+    const uint32_t* wv = sm.wv[threadIdx.x >> 5];
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&sm.nt_cnt, n);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (uint32_t i = lane; i < n; i += 32) {
+        const uint32_t at = base + i;
+        if (at < I.n) I.touched[at] = wv[i];
+        else fail(ctl, 7);
+    }
+    __syncwarp();
+    wc = 0;
+}
+
 // Comparator accumulator key of frontier column j at level k: the high word is
 // a stamp that decreases with k (and stays below the all-ones initial value),
 // so one atomicMin both overwrites stale keys and keeps the least j.
@@ -434,22 +554,48 @@ struct Tally {
 // the per-entry step: mask, multiply, claim -- kIlp entries per thread at once
 // ---------------------------------------------------------------------------
 
-// Entries (r[u] in column j[u]) where act[u], at level k.  Each stage issues
+// How a level claims the vertices it reaches.
+enum ClaimVar : int {
+    kVarWide = 0,    // atomicMin with return; the winner stages the vertex (frontier blocks)
+    kVarNarrow = 1,  // the same inside a resident narrow run (plain frontier list)
+    kVarScan = 2,    // reductions only: atomicMin and the bit in the write bitmap without
+                     // return; an extraction phase collects the new vertices afterwards
+};
+
+// Entries (r[u] in column j[u]; r[u] == kUnset: none) at level k.  Each stage issues
 // kIlp independent memory operations before consuming any.  Submatrix mode
 // appends the vertices of level k+1 to the next frontier; comparator mode
 // appends first-touched rows to the touched list.  All 32 lanes must call.
-template <int MODE>
+template <int MODE, int VAR>
 __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const EngineParams& P,
                                               Smem& sm, uint32_t k, const uint32_t (&r)[kIlp],
-                                              const uint32_t (&j)[kIlp], const bool (&act)[kIlp],
-                                              Tally& t, uint32_t& wc) {
+                                              const uint32_t (&j)[kIlp], Tally& t, uint32_t& wc) {
     const uint32_t p = k & 1;
     if (MODE == kModeSub) {
         const uint32_t* test_bm = I.bm[p];
         uint32_t* write_bm = I.bm[p ^ 1];
         uint32_t w[kIlp];
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) w[u] = act[u] ? ld_frozen(test_bm + (r[u] >> 5)) : 0xFFFFFFFFu;
+        for (int u = 0; u < kIlp; ++u)
+            w[u] = r[u] != kUnset
+                       ? (VAR == kVarNarrow ? ld_l2(test_bm + (r[u] >> 5))
+                                            : ld_frozen(test_bm + (r[u] >> 5)))
+                       : 0xFFFFFFFFu;
+        if (VAR == kVarScan) {
+            // the (min, index) product and the claim bit as reductions: the
+            // least column still wins, and the new vertices are read off the
+            // bitmaps once the level is complete
+#pragma unroll
+            for (int u = 0; u < kIlp; ++u) {
+                if (!((w[u] >> (r[u] & 31)) & 1u)) {
+                    ++t.unmasked;
+                    ++t.claims;
+                    atomicMin(I.parent + r[u], j[u]);
+                    atomicOr(write_bm + (r[u] >> 5), 1u << (r[u] & 31));
+                }
+            }
+            return;
+        }
         // rows outside V_{k+1} are masked before the multiply; the (min, index)
         // product is an atomicMin of j into parent[r], and moving parent[r]
         // off "unset" claims r for level k+1
@@ -477,16 +623,23 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             old[u] = 0ull;
-            if (act[u]) {
+            if (r[u] != kUnset) {
                 ++t.unmasked;
                 ++t.claims;
                 old[u] = atomicMin(I.y + r[u], plain_key(k, j[u]));
             }
         }
         // first touch of row r at this level: it goes to the touched list
+        // (narrow runs stage it with the warp's other appends)
+        if (VAR == kVarNarrow) {
+#pragma unroll
+            for (int u = 0; u < kIlp; ++u)
+                stage_warp(r[u] != kUnset && (uint32_t)(old[u] >> 32) != plain_stamp(k), r[u], sm, wc);
+            return;
+        }
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
-            const bool first = act[u] && (uint32_t)(old[u] >> 32) != plain_stamp(k);
+            const bool first = r[u] != kUnset && (uint32_t)(old[u] >> 32) != plain_stamp(k);
             const uint32_t mask = __ballot_sync(0xFFFFFFFFu, first);
             if (mask) {
                 const uint32_t lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
@@ -540,11 +693,14 @@ __device__ __forceinline__ void stats_flush(Smem& sm, InstCtl* ctl) {
 // slots per group (coalesced row loads) and kIlp groups per step.  The vertex
 // of slot s is a prefix count of vertex starts, read from sm.sbits with one
 // popcount.  The row loads of step s+1 are issued before step s is processed.
-template <int MODE>
-__device__ void expand_slots(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                             uint32_t cnt, uint32_t l0, uint32_t l1, uint32_t mat, uint32_t k,
-                             Tally& t) {
+template <int MODE, int VAR>
+__device__ __forceinline__ void expand_core(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+                             uint32_t cnt, uint32_t l0, uint32_t l1, uint32_t mat,
+                             uint32_t mat_next, uint32_t k, Tally& t) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#ifdef ABFS_EXPAND_PROFILE
+    const long long xt0 = sm.prof_on ? clock64() : 0ll;
+#endif
     const uint32_t span = l1 - l0;
     const uint32_t per = (span + kWarps - 1) / kWarps;
     const uint32_t e0 = l0 + min(span, warp * per);
@@ -564,10 +720,9 @@ __device__ void expand_slots(const Inst& I, InstCtl* ctl, const EngineParams& P,
         vb = lo - (sm.off[lo] == e0 ? 1u : 0u);
     }
     uint32_t starts = 0;  // vertex starts in [e0, current group base)
+    // row index (kUnset: no entry in this slot) and frontier column of each group
     uint32_t r[kIlp], j[kIlp];
-    bool act[kIlp];
-    auto load_step = [&](uint32_t base, uint32_t (&rr)[kIlp], uint32_t (&jj)[kIlp],
-                         bool (&aa)[kIlp]) {
+    auto load_step = [&](uint32_t base, uint32_t (&rr)[kIlp], uint32_t (&jj)[kIlp]) {
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             const uint32_t gb = base + 32 * u;
@@ -578,63 +733,103 @@ __device__ void expand_slots(const Inst& I, InstCtl* ctl, const EngineParams& P,
             const uint32_t s = gb + lane;
             const uint32_t v = vb + starts + __popc(w & le_mask);
             starts += __popc(w);
-            aa[u] = false;
-            rr[u] = 0;
+            rr[u] = kUnset;
             jj[u] = 0;
             if (s < e1 && s < sm.end[v]) {
-                aa[u] = true;
                 jj[u] = sm.v[v];
                 rr[u] = ld_row(rows, sm.b[v] + s, mat, pol);
             }
         }
     };
     uint32_t wc = sm.wcnt[warp];
-    const uint32_t mat_next = mat_for_level(ctl, k + 1);
-    if (e0 < e1) load_step(e0, r, j, act);
+    if (e0 < e1) load_step(e0, r, j);
+#ifdef ABFS_EXPAND_PROFILE
+    long long xt1 = 0, xflush = 0, xproc = 0;
+    if (sm.prof_on) xt1 = clock64();
+#endif
     for (uint32_t base = e0; base < e1; base += 32 * kIlp) {
         uint32_t r2[kIlp], j2[kIlp];
-        bool act2[kIlp];
         if (base + 32 * kIlp < e1) {
-            load_step(base + 32 * kIlp, r2, j2, act2);
+            load_step(base + 32 * kIlp, r2, j2);
         } else {
 #pragma unroll
             for (int u = 0; u < kIlp; ++u) {
-                act2[u] = false;
-                r2[u] = j2[u] = 0;
+                r2[u] = kUnset;
+                j2[u] = 0;
             }
         }
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) t.read += act[u];
-        process_group<MODE>(I, ctl, P, sm, k, r, j, act, t, wc);
-        if (MODE == kModeSub && wc > (uint32_t)kWarpFlushAt)
+        for (int u = 0; u < kIlp; ++u) t.read += (r[u] != kUnset);
+#ifdef ABFS_EXPAND_PROFILE
+        const long long xp0 = sm.prof_on ? clock64() : 0ll;
+#endif
+        process_group<MODE, VAR>(I, ctl, P, sm, k, r, j, t, wc);
+#ifdef ABFS_EXPAND_PROFILE
+        const long long xp1 = sm.prof_on ? clock64() : 0ll;
+        xproc += xp1 - xp0;
+#endif
+        if (VAR == kVarScan) {
+            // nothing staged
+        } else if (VAR == kVarNarrow) {
+            if (wc > (uint32_t)kWarpFlushAt) {
+                if (MODE == kModeSub) narrow_append(sm, I, ctl, (k + 1) & 1, mat_next, wc);
+                else narrow_touch(sm, I, ctl, wc);
+            }
+        } else if (MODE == kModeSub && wc > (uint32_t)kWarpFlushAt) {
             warp_flush(sm, I, ctl, P, (k + 1) & 1, mat_next, wc);
+        }
+#ifdef ABFS_EXPAND_PROFILE
+        if (sm.prof_on) xflush += clock64() - xp1;
+#endif
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             r[u] = r2[u];
             j[u] = j2[u];
-            act[u] = act2[u];
         }
     }
     if (lane == 0) sm.wcnt[warp] = wc;
+#ifdef ABFS_EXPAND_PROFILE
+    // per-warp accounting, in builds made for profiling the expand loop
+    if (sm.prof_on && lane == 0) {
+        const long long xt2 = clock64();
+        atomicAdd(&sm.prof[kProfXSetup], (unsigned long long)(xt1 - xt0));
+        atomicAdd(&sm.prof[kProfXProcess], (unsigned long long)xproc);
+        atomicAdd(&sm.prof[kProfXFlush], (unsigned long long)xflush);
+        atomicAdd(&sm.prof[kProfXLoop], (unsigned long long)(xt2 - xt1));
+        atomicAdd(&sm.prof[kProfXCalls], 1ull);
+    }
+#endif
     __syncwarp();
 }
 
-// Unit u of the level-k frontier: entry slots [u*U, min((u+1)*U, total)).
-// The unit walks the frontier blocks in entry order from the vertex recorded
-// in ustart[u], staging up to `tile` vertices from up to 32 blocks at a time.
-template <int MODE>
-__device__ void unit_level(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                           uint32_t k, uint32_t u) {
+// The expand loop of wide units, compiled as a function of its own.
+template <int MODE, int VAR>
+__device__ ABFS_NOINLINE void expand_slots(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                           Smem& sm, uint32_t cnt, uint32_t l0, uint32_t l1,
+                                           uint32_t mat, uint32_t mat_next, uint32_t k, Tally& t) {
+    expand_core<MODE, VAR>(I, ctl, P, sm, cnt, l0, l1, mat, mat_next, k, t);
+}
+
+// Unit u of the level-k frontier: entry slots [u*U, min((u+1)*U, total)) with
+// U = m granules of P.unit slots (m is chosen per level).  The unit walks the
+// frontier blocks in entry order from the vertex recorded in the unit start of
+// its first granule, staging up to `tile` vertices from up to 32 blocks at a
+// time.
+template <int MODE, int VAR>
+__device__ ABFS_NOINLINE void unit_level(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+                           uint32_t k, uint32_t u, uint32_t m) {
     const uint32_t p = k & 1;
     const unsigned long long bc = ld_relaxed64(&ctl->bctr[p]);
+    uint32_t mat, mat_next;
+    level_mats(ctl, k, mat, mat_next);
     const unsigned long long total = bc >> kBlockBits;
     const uint32_t nb = (uint32_t)(bc & kBlockMask);
-    const unsigned long long u_lo = (unsigned long long)u * P.unit;
-    const unsigned long long u_hi = min(total, u_lo + P.unit);
-    const uint32_t mat = mat_for_level(ctl, k);
+    const unsigned long long U = (unsigned long long)P.unit * m;
+    const unsigned long long u_lo = (unsigned long long)u * U;
+    const unsigned long long u_hi = min(total, u_lo + U);
     const Block* blk = I.blk[p];
     if (threadIdx.x == 0) {
-        const uint2 st = ld_l2(I.ustart[p] + u);
+        const uint2 st = ld_l2(I.ustart[p] + (unsigned long long)u * m);
         sm.cur_b = st.x;
         sm.cur_i = st.y;
     }
@@ -740,7 +935,8 @@ __device__ void unit_level(const Inst& I, InstCtl* ctl, const EngineParams& P, S
         const unsigned long long s_hi = min(u_hi, (unsigned long long)sm.sub_end);
         const long long pt1 = prof_now(sm);
         prof_add(sm, kProfGather, pt0);
-        expand_slots<MODE>(I, ctl, P, sm, cnt, (uint32_t)(e - g0), (uint32_t)(s_hi - g0), mat, k, t);
+        expand_slots<MODE, VAR>(I, ctl, P, sm, cnt, (uint32_t)(e - g0), (uint32_t)(s_hi - g0), mat,
+                                mat_next, k, t);
         const long long pt2 = prof_now(sm);
         prof_add(sm, kProfExpand, pt1);
         e = s_hi;
@@ -752,17 +948,18 @@ __device__ void unit_level(const Inst& I, InstCtl* ctl, const EngineParams& P, S
     if ((threadIdx.x & 31) == 0 && nnz_local) atomicAdd(&sm.st_nnz, (unsigned long long)nnz_local);
     tally_flush(sm, t);
     const long long pt3 = prof_now(sm);
-    if (MODE == kModeSub) cta_flush(sm, I, ctl, P, p ^ 1, mat_for_level(ctl, k + 1));
+    if (MODE == kModeSub && VAR != kVarScan) cta_flush(sm, I, ctl, P, p ^ 1, mat_next);
     prof_add(sm, kProfFlush, pt3);
 }
 
 // Comparator: apply the visited mask to a tile of touched rows of level k.
-__device__ void unit_plain_mask(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+__device__ ABFS_NOINLINE void unit_plain_mask(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                                 uint32_t k, uint32_t tile_idx, uint32_t ntouched) {
     const uint32_t pn = (k + 1) & 1;
     const uint32_t base = tile_idx * P.tile;
     const uint32_t cnt = min(P.tile, ntouched - base);
-    const uint32_t mat_next = mat_for_level(ctl, k + 1);
+    uint32_t mat, mat_next;
+    level_mats(ctl, k, mat, mat_next);
     uint32_t wc = sm.wcnt[threadIdx.x >> 5];
     for (uint32_t b0 = 0; b0 < cnt; b0 += kThreads) {
         const uint32_t t = b0 + threadIdx.x;
@@ -784,12 +981,48 @@ __device__ void unit_plain_mask(const Inst& I, InstCtl* ctl, const EngineParams&
     cta_flush(sm, I, ctl, P, pn, mat_next);
 }
 
+// Vertices per extraction unit: one bitmap word per thread.
+constexpr uint32_t kExtractWords = kThreads;
+
+// Extraction after a level k whose claims were reductions: the vertices of
+// level k+1 are the bits of the write bitmap that the test bitmap lacks
+// (V_{k+1} minus V_{k+2} in the paper's terms).  Unit u covers bitmap words
+// [u*kExtractWords, ...); each warp hands its 32 words' new vertices to the
+// frontier blocks of level k+1.  Their parents are already final.
+__device__ ABFS_NOINLINE void unit_extract(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+                             uint32_t k, uint32_t u) {
+    const uint32_t p = k & 1, pn = p ^ 1;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t mat, mat_next;
+    level_mats(ctl, k, mat, mat_next);
+    const uint32_t w0 = u * kExtractWords + warp * 32;
+    const uint32_t wi = w0 + lane;
+    uint32_t fresh = 0;
+    if (wi < I.nwords) fresh = ld_l2(I.bm[pn] + wi) & ~ld_l2(I.bm[p] + wi);
+    uint32_t wc = sm.wcnt[warp];
+    uint32_t claims = 0;
+    for (uint32_t q = 0; q < 32; ++q) {
+        const uint32_t bits = __shfl_sync(0xFFFFFFFFu, fresh, q);
+        if (!bits) continue;
+        const bool want = (bits >> lane) & 1u;
+        const uint32_t v = (w0 + q) * 32 + lane;
+        if (want) I.level[v] = (int32_t)(k + 1);
+        stage_warp(want, v, sm, wc);
+        if (wc > (uint32_t)(kWarpBuf - 32)) warp_flush(sm, I, ctl, P, pn, mat_next, wc);
+        claims += want;
+    }
+    (void)claims;
+    if (lane == 0) sm.wcnt[warp] = wc;
+    __syncwarp();
+    cta_flush(sm, I, ctl, P, pn, mat_next);
+}
+
 // Shrink: compacts the unvisited columns among vertices
 // [u*shrink_tile, (u+1)*shrink_tile) to their unvisited rows (A_k = S_k A S_k
 // restricted to the columns still to be multiplied).  `vis` holds the
 // vertices reached so far; src_mat is the matrix those columns are read from
 // and dst (1 or 2) the shrunk copy being written.
-__device__ void unit_shrink(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+__device__ ABFS_NOINLINE void unit_shrink(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                             uint32_t u, const uint32_t* vis, uint32_t src_mat, uint32_t dst) {
     const uint32_t v0 = u * P.shrink_tile;
     const uint32_t cnt = min(P.shrink_tile, I.n - v0);
@@ -867,7 +1100,7 @@ __device__ void unit_shrink(const Inst& I, InstCtl* ctl, const EngineParams& P, 
 // Serving: clears the outputs (and bitmaps) of vertices [u*init_tile, ...) of
 // a newly started search -- the work the initialisation kernels do for
 // abfs_run, done inside the long-lived launch.
-__device__ void unit_init(const Inst& I, const EngineParams& P, uint32_t u) {
+__device__ ABFS_NOINLINE void unit_init(const Inst& I, const EngineParams& P, uint32_t u) {
     const uint32_t v0 = u * P.init_tile;
     const uint32_t v1 = min(I.n, v0 + P.init_tile);
     for (uint32_t v = v0 + threadIdx.x; v < v1; v += kThreads) {
@@ -900,15 +1133,19 @@ __device__ void run_unit(const Inst& I, InstCtl* ctl, const EngineParams& P, Sme
         unit_shrink(I, ctl, P, sm, unit, I.bm[(k + 1) & 1], src_mat, /*dst=*/nitems);
     } else if (kind == kPhPlainMask) {
         unit_plain_mask(I, ctl, P, sm, k, unit, nitems);
+    } else if (kind == kPhExtract) {
+        unit_extract(I, ctl, P, sm, k, unit);
+    } else if (MODE == kModeSub && kind == kPhLevelScan) {
+        unit_level<MODE, kVarScan>(I, ctl, P, sm, k, unit, nitems);
     } else {
-        unit_level<MODE>(I, ctl, P, sm, k, unit);
+        unit_level<MODE, kVarWide>(I, ctl, P, sm, k, unit, nitems);
     }
     stats_flush(sm, ctl);
 }
 
 // Optional per-phase trace entry: [time lo, time hi, kind<<24 | level, alone]
 // and [items, vertices, entries (low 32 bits), 0].
-__device__ void trace_put(const Inst& I, InstCtl* ctl, uint32_t kind, uint32_t level,
+__device__ ABFS_NOINLINE void trace_put(const Inst& I, InstCtl* ctl, uint32_t kind, uint32_t level,
                           uint32_t alone, uint32_t ni, uint32_t nf, unsigned long long ne) {
     const uint32_t tn = ld_relaxed(&ctl->trace_n);
     if (tn >= I.trace_cap) return;
@@ -919,10 +1156,264 @@ __device__ void trace_put(const Inst& I, InstCtl* ctl, uint32_t kind, uint32_t l
     st_relaxed(&ctl->trace_n, tn + 1);
 }
 
+// Whether the i-th physical shrink (i = shrinks + 1) is due once `reached`
+// vertices are reached: it waits until a fraction 1-(1-theta)^i of n is reached.
+__device__ __forceinline__ bool shrink_due(const EngineParams& P, uint32_t reached, uint32_t n,
+                                           uint32_t shrinks) {
+    if (!(P.shrink_theta > 0.f && P.shrink_theta < 1.f) || shrinks >= P.shrink_max) return false;
+    const float frac = (float)reached / (float)n;
+    const float need = 1.f - powf(1.f - P.shrink_theta, (float)(shrinks + 1));
+    return frac >= need;
+}
+
+// ---------------------------------------------------------------------------
+// resident narrow runs
+// ---------------------------------------------------------------------------
+// While a search's frontier stays within narrow_max vertices and narrow_edges
+// slots, one CTA runs its levels back to back without the block bookkeeping of
+// wide levels.  The frontier of level k is a plain list at fq/fbeg/fpre[k&1]:
+// vertex, column begin and column length.  Claims gather in the warp staging
+// buffers and are appended with a shared-memory counter; the reached count
+// and the level stay in shared memory until the run ends.  The run ends when
+// the frontier empties, outgrows the narrow bounds, or a shrink is due; the
+// last frontier is then rewritten as blocks and the general path decides what
+// follows.
+
+// Expands the f vertices of the level-k list (lens: fbeg/fpre hold column
+// begins and lengths in matrix mat; otherwise only the ids are valid and the
+// columns are looked up) in chunks of up to `tile` vertices and windows of up
+// to kUnitMax slots.  Whole CTA.
+template <int MODE>
+__device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+                              uint32_t k, uint32_t f, bool lens, uint32_t mat, uint32_t mat_next,
+                              Tally& t, uint32_t& nnz_local) {
+    const uint32_t p = k & 1;
+    for (uint32_t c0 = 0; c0 < f; c0 += P.tile) {
+        const long long pt0 = prof_now(sm);
+        const uint32_t cnt = min(P.tile, f - c0);
+        for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
+            const uint32_t v = ld_l2(I.fq[p] + c0 + s);
+            uint32_t beg, len;
+            if (lens) {
+                beg = ld_l2(I.fbeg[p] + c0 + s);
+                len = ld_l2(I.fpre[p] + c0 + s);
+            } else {
+                const ColRef c = col_of(I, mat, v);
+                beg = c.beg;
+                len = c.len;
+            }
+            sm.v[s] = v;
+            sm.b[s] = beg;
+            sm.off[s] = len + kVertexSlots;
+            // the frontier joins the visited set of the next level's test
+            if (MODE == kModeSub) atomicOr(I.bm[p ^ 1] + (v >> 5), 1u << (v & 31));
+            nnz_local += (mat == 0) ? len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
+        }
+        for (uint32_t w = threadIdx.x; w < (uint32_t)kStartWords; w += kThreads) sm.sbits[w] = 0u;
+        __syncthreads();
+        block_exclusive_scan<kTileItems>(sm.off, cnt, sm);
+        const uint32_t S = sm.off[cnt];
+        // window [l0, l1) of at most kUnitMax slots; its vertex starts in sbits
+        uint32_t l0 = 0, l1 = min(S, kUnitMax);
+        for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
+            const uint32_t st = sm.off[s];
+            sm.end[s] = sm.off[s + 1] - kVertexSlots;
+            sm.b[s] -= st;  // row index of slot x is b + x
+            if (st < l1) atomicOr(&sm.sbits[st >> 5], 1u << (st & 31));
+        }
+        __syncthreads();
+        prof_add(sm, kProfNLoad, pt0);
+        for (;;) {
+            const long long pt1 = prof_now(sm);
+            expand_core<MODE, kVarNarrow>(I, ctl, P, sm, cnt, l0, l1, mat, mat_next, k, t);
+            __syncthreads();
+            prof_add(sm, kProfNExpand, pt1);
+            if (l1 >= S) break;
+            l0 = l1;
+            l1 = min(S, l0 + kUnitMax);
+            for (uint32_t w = threadIdx.x; w < (uint32_t)kStartWords; w += kThreads) sm.sbits[w] = 0u;
+            __syncthreads();
+            for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
+                const uint32_t st = sm.off[s];
+                if (st >= l0 && st < l1) atomicOr(&sm.sbits[(st - l0) >> 5], 1u << ((st - l0) & 31));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Rewrites the list of parity pn (fn vertices; fpre holds column lengths) as
+// frontier blocks of up to kThreads*8 vertices: slot offsets within the block,
+// unit starts, and the parity's counters.  Whole CTA.
+__device__ ABFS_NOINLINE void narrow_to_blocks(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+                                 uint32_t pn, uint32_t fn) {
+    constexpr uint32_t kItems = 8;
+    constexpr uint32_t kChunk = kThreads * kItems;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long eb = 0;
+    uint32_t nb = 0;
+    for (uint32_t c0 = 0; c0 < fn; c0 += kChunk, ++nb) {
+        const uint32_t cnt = min(kChunk, fn - c0);
+        uint32_t x[kItems];
+        uint32_t sum = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < kItems; ++q) {
+            const uint32_t idx = tid * kItems + q;
+            x[q] = idx < cnt ? ld_l2(I.fpre[pn] + c0 + idx) + kVertexSlots : 0u;
+            sum += x[q];
+        }
+        const uint32_t incl = warp_incl_scan(sum);
+        if (lane == 31) sm.warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = lane < (uint32_t)kWarps ? sm.warp_sums[lane] : 0u;
+            const uint32_t wi = warp_incl_scan(w);
+            if (lane < (uint32_t)kWarps) sm.warp_sums[lane] = wi - w;
+            if (lane == kWarps - 1) sm.warp_sums[kWarps] = wi;
+        }
+        __syncthreads();
+        uint32_t run = sm.warp_sums[warp] + incl - sum;
+        const uint32_t total = sm.warp_sums[kWarps];
+        const bool ok = nb < I.bcap && nb < kBlockMask;
+        for (uint32_t q = 0; q < kItems; ++q) {
+            const uint32_t idx = tid * kItems + q;
+            if (idx < cnt && ok) I.fpre[pn][c0 + idx] = run;
+            warp_unit_starts(I, ctl, P, pn, nb, idx, eb + run, (idx < cnt && ok) ? x[q] : 0u);
+            run += x[q];
+        }
+        if (tid == 0) {
+            if (ok) {
+                Block* B = I.blk[pn] + nb;
+                B->vb = c0;
+                B->nv = cnt;
+                B->eb = eb;
+            } else {
+                fail(ctl, 7);
+            }
+        }
+        eb += total;
+        __syncthreads();  // warp_sums is reused
+    }
+    if (tid == 0) {
+        st_relaxed64(&ctl->bctr[pn], (eb << kBlockBits) | (unsigned long long)nb);
+        st_relaxed(&ctl->fcnt[pn], fn);
+    }
+}
+
+// Runs levels k, k+1, ... of the current search on this CTA (the frontier of
+// level k is in the parity's blocks, its ids contiguous at fq[k&1]).  Returns
+// the last level run; its successor frontier is left in block form with the
+// search's counters set as the general path expects.  Whole CTA.
+template <int MODE>
+__device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+                               uint32_t k, unsigned long long* heartbeat) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        // the matrices change only at shrinks, which end a run
+        sm.nr_f = ld_relaxed(&ctl->fcnt[k & 1]);
+        sm.nr_reached = ld_relaxed(&ctl->reached);
+        sm.nr_shrinks = ld_relaxed(&ctl->shrinks);
+        sm.nr_sw = ld_relaxed(&ctl->mat_switch);
+        sm.nr_mcur = ld_relaxed(&ctl->mat_cur);
+        sm.nr_mprev = ld_relaxed(&ctl->mat_prev);
+        sm.nq_cnt = 0;
+        sm.nt_cnt = 0;
+        sm.nq_slots = 0;
+    }
+    __syncthreads();
+    const uint32_t sw = sm.nr_sw, mat_cur = sm.nr_mcur, mat_prev = sm.nr_mprev;
+    bool lens = false;
+    for (;;) {
+        const uint32_t pn = (k + 1) & 1;
+        const uint32_t f = sm.nr_f;
+        const uint32_t mat = k >= sw ? mat_cur : mat_prev;
+        const uint32_t mat_next = k + 1 >= sw ? mat_cur : mat_prev;
+        // issued now, read when the level ends
+        const uint32_t err = threadIdx.x == 0 ? ld_relaxed(&ctl->err) : 0u;
+        Tally t;
+        uint32_t nnz_local = 0;
+        narrow_expand<MODE>(I, ctl, P, sm, k, f, lens, mat, mat_next, t, nnz_local);
+        const long long pt2 = prof_now(sm);
+        {
+            // the warps' leftovers
+            uint32_t wc = sm.wcnt[warp];
+            if (wc) {
+                if (MODE == kModeSub) narrow_append(sm, I, ctl, pn, mat_next, wc);
+                else narrow_touch(sm, I, ctl, wc);
+            }
+            if (lane == 0) sm.wcnt[warp] = 0;
+        }
+        __syncthreads();
+        if (MODE == kModePlain) {
+            // comparator mask: touched rows not yet reached join level k+1 with
+            // the least column of the accumulator
+            const uint32_t T = sm.nt_cnt;
+            uint32_t wc = 0;
+            for (uint32_t b0 = 0; b0 < T; b0 += kThreads) {
+                const uint32_t i = b0 + threadIdx.x;
+                bool want = false;
+                uint32_t r = 0;
+                if (i < T) {
+                    r = ld_l2(I.touched + i);
+                    if ((int32_t)ld_l2((const uint32_t*)I.level + r) == -1) {
+                        const unsigned long long y = ld_l2(I.y + r);
+                        I.level[r] = (int32_t)(k + 1);
+                        I.parent[r] = (uint32_t)(y & 0xFFFFFFFFull);
+                        want = true;
+                    }
+                }
+                stage_warp(want, r, sm, wc);
+                if (wc > (uint32_t)(kWarpBuf - 32)) narrow_append(sm, I, ctl, pn, mat_next, wc);
+            }
+            if (wc) narrow_append(sm, I, ctl, pn, mat_next, wc);
+            __syncthreads();
+        }
+        const long long pt3 = prof_now(sm);
+        prof_add(sm, kProfNAppend, pt2);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) nnz_local += __shfl_xor_sync(0xFFFFFFFFu, nnz_local, d);
+        if (lane == 0 && nnz_local) atomicAdd(&sm.st_nnz, (unsigned long long)nnz_local);
+        tally_flush(sm, t);
+        if (threadIdx.x == 0) {
+            const uint32_t fn = sm.nq_cnt;
+            const unsigned long long slots = sm.nq_slots;
+            sm.nq_cnt = 0;
+            sm.nt_cnt = 0;
+            sm.nq_slots = 0;
+            uint32_t stop = 0;
+            if (fn == 0 || err != 0 || fn > P.narrow_max || slots > P.narrow_edges)
+                stop = 1;
+            else if (MODE == kModeSub && shrink_due(P, sm.nr_reached + fn, I.n, sm.nr_shrinks))
+                stop = 1;
+            if (!stop) {
+                sm.nr_reached += fn;
+                if (I.trace)
+                    trace_put(I, ctl, MODE == kModePlain ? kPhPlainMult : kPhLevel, k + 1, 2u, 0u, fn,
+                              slots);
+            }
+            sm.nr_stop = stop;
+            sm.nr_f = fn;
+            atomicAdd(heartbeat, 1ull);
+            if (sm.prof_on) sm.prof[kProfNLevels] += 1;
+        }
+        __syncthreads();
+        prof_add(sm, kProfNDecide, pt3);
+        if (sm.nr_stop) break;
+        lens = true;
+        ++k;
+    }
+    const long long pt4 = prof_now(sm);
+    narrow_to_blocks(I, ctl, P, sm, (k + 1) & 1, sm.nr_f);
+    if (threadIdx.x == 0) st_relaxed(&ctl->reached, sm.nr_reached);
+    stats_flush(sm, ctl);
+    prof_add(sm, kProfNBlocks, pt4);
+    return k;
+}
+
 // Thread 0 of the advancing CTA: the phase that follows (kind, k), written to
 // sm.cmd; sm.cmd.quit = 1 when the search is over.
 template <int MODE>
-__device__ void decide_next(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+__device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                             uint32_t kind, uint32_t k, uint32_t* done_count) {
     uint32_t nkind = 0, nk = 0, ni = 0, finish = 0;
     if (kind == kPhInit) {
@@ -946,6 +1437,10 @@ __device__ void decide_next(const Inst& I, InstCtl* ctl, const EngineParams& P, 
         st_relaxed(&ctl->reached, 1u);
         nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
         nk = 0;
+    } else if (kind == kPhLevelScan) {
+        // the new vertices of a level claimed by reductions are read off the bitmaps
+        nkind = kPhExtract;
+        nk = k;
     } else if (kind == kPhPlainMult) {
         // comparator: the mask phase of the same level follows the multiply
         const uint32_t t = ld_relaxed(&ctl->tcnt);
@@ -984,14 +1479,8 @@ __device__ void decide_next(const Inst& I, InstCtl* ctl, const EngineParams& P, 
             st_relaxed(&ctl->shrinks, shrinks);
         }
         if (!finish) {
-            bool do_shrink = false;
-            if (MODE == kModeSub && kind != kPhShrink && P.shrink_theta > 0.f &&
-                P.shrink_theta < 1.f && shrinks < P.shrink_max) {
-                // the i-th shrink waits until a fraction 1-(1-theta)^i of n is reached
-                const float frac = (float)reached / (float)I.n;
-                const float need = 1.f - powf(1.f - P.shrink_theta, (float)(shrinks + 1));
-                do_shrink = frac >= need;
-            }
+            const bool do_shrink =
+                MODE == kModeSub && kind != kPhShrink && shrink_due(P, reached, I.n, shrinks);
             if (do_shrink) {
                 // alternate copies so the frontier of level k+1 keeps its matrix
                 const uint32_t cur = ld_relaxed(&ctl->mat_cur);
@@ -1045,7 +1534,9 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
             if (I.trace && threadIdx.x == 0) trace_put(I, ctl, 0xFFu, k, 0u, 0u, 0u, 0ull);
             return;
         }
-        const uint32_t nkind = sm.cmd.kind, nk = sm.cmd.level, ni = sm.cmd.nitems;
+        const uint32_t nk = sm.cmd.level;
+        uint32_t nkind = sm.cmd.kind;
+        uint32_t ni = sm.cmd.nitems;
         uint32_t units, nf = 0;
         unsigned long long ne = 0;
         bool alone;
@@ -1055,14 +1546,26 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
         } else if (nkind == kPhPlainMask) {
             units = (ni + P.tile - 1) / P.tile;
             alone = ni <= P.narrow_max;
+        } else if (nkind == kPhExtract) {
+            units = (I.nwords + kExtractWords - 1) / kExtractWords;
+            alone = units <= 1;
         } else {
-            // a level (or the comparator's multiply) over the frontier of level nk
+            // a level (or the comparator's multiply) over the frontier of level nk;
+            // its units are m granules, about two per CTA of the grid (ni = m)
             ne = ld_relaxed64(&ctl->bctr[nk & 1]) >> kBlockBits;
             nf = ld_relaxed(&ctl->fcnt[nk & 1]);
-            units = (uint32_t)((ne + P.unit - 1) / P.unit);
+            const unsigned long long mmax = kUnitMax / P.unit;
+            unsigned long long m = ne / ((unsigned long long)P.unit * 2ull * gridDim.x);
+            m = m < 1ull ? 1ull : (m > mmax ? mmax : m);
+            ni = (uint32_t)m;
+            units = (uint32_t)((ne + P.unit * m - 1) / (P.unit * m));
             alone = nf <= P.narrow_max && ne <= P.narrow_edges;
+            // a large level claims by reductions and a bitmap scan
+            if (MODE == kModeSub && nkind == kPhLevel && !alone && P.scan_min && ne >= P.scan_min)
+                nkind = kPhLevelScan;
         }
-        if (I.trace && threadIdx.x == 0) trace_put(I, ctl, nkind, nk, alone, ni, nf, ne);
+        if (I.trace && threadIdx.x == 0)
+            trace_put(I, ctl, nkind, nk, alone, nkind == kPhPlainMask ? ni : units, nf, ne);
         if (!alone) {
             if (threadIdx.x == 0) {
                 const uint32_t e = ld_relaxed(&ctl->epoch) + 1;
@@ -1080,6 +1583,14 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
             }
             __syncthreads();
             return;
+        }
+        if (P.narrow_loop && (nkind == kPhLevel || nkind == kPhPlainMult)) {
+            // a resident run of narrow levels on this CTA
+            k = narrow_run<MODE>(I, ctl, P, sm, nk, heartbeat);
+            kind = kPhLevel;
+            __threadfence();
+            __syncthreads();
+            continue;
         }
         // narrow: this CTA runs every unit of the phase, then decides again
         for (uint32_t u = 0; u < units; ++u) run_unit<MODE>(I, ctl, P, sm, nkind, nk, u, ni);
@@ -1137,22 +1648,35 @@ __device__ __forceinline__ bool take_unit(const EngineArgs& a, uint32_t q, Smem&
 }
 
 // Serving: the CTA that claimed a submitted search resets its control block
-// and publishes the initialisation phase (epoch 0).  Whole CTA.
-__device__ void start_search(const EngineArgs& a, Smem& sm) {
+// and publishes the initialisation phase.  The slot's epoch sequence goes on
+// from the previous search instead of restarting: a CTA that looked at the
+// slot during the previous search may still add to `grab` late, and with a
+// fresh epoch that stale grab can never match the new phase's descriptor.
+// Whole CTA.
+__device__ ABFS_NOINLINE void start_search(const EngineArgs& a, Smem& sm) {
     const Inst& I = sm.I;
     InstCtl* ctl = I.ctl;
     uint32_t* c = reinterpret_cast<uint32_t*>(ctl);
-    for (uint32_t w = threadIdx.x; w < sizeof(InstCtl) / 4; w += kThreads) c[w] = 0u;  // status: idle
+    // everything but grab, desc[] and epoch is cleared (status: idle)
+    const uint32_t keep_lo = offsetof(InstCtl, grab) / 4, keep_hi = offsetof(InstCtl, bctr) / 4;
+    const uint32_t keep_ep = offsetof(InstCtl, epoch) / 4;
+    for (uint32_t w = threadIdx.x; w < sizeof(InstCtl) / 4; w += kThreads)
+        if ((w < keep_lo || w >= keep_hi) && w != keep_ep) c[w] = 0u;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t units = (I.n + a.p.init_tile - 1) / a.p.init_tile;
-        st_relaxed(&ctl->kind[0], kPhInit);
-        st_relaxed(&ctl->pending[0], units);
-        ctl->desc[1] = ~0ull;
+        const uint32_t e = ld_relaxed(&ctl->epoch) + 1;
+        const uint32_t q = e & 1;
+        st_relaxed(&ctl->kind[q], kPhInit);
+        st_relaxed(&ctl->plevel[q], 0u);
+        st_relaxed(&ctl->nitems[q], 0u);
+        st_relaxed(&ctl->pending[q], units);
+        st_relaxed(&ctl->epoch, e);
         __threadfence();
-        atomicExch(&ctl->desc[0], (unsigned long long)units);
-        atomicExch(&ctl->grab, 0ull);
+        atomicExch(&ctl->desc[q], ((unsigned long long)e << 32) | units);
+        __threadfence();
+        atomicExch(&ctl->grab, (unsigned long long)e << 32);
         __threadfence();
         st_relaxed(&ctl->status, kRunning);
         atomicAdd(a.heartbeat, 1ull);
@@ -1223,7 +1747,7 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 2) engine_kernel(EngineArgs a) {
+__global__ void __launch_bounds__(kThreads, kMinCtas) engine_kernel(EngineArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     if (threadIdx.x == 0) {
@@ -1272,7 +1796,7 @@ __global__ void __launch_bounds__(kThreads, 2) engine_kernel(EngineArgs a) {
                 }
             }
             __nanosleep(backoff);
-            if (backoff < 2048) backoff <<= 1;
+            if (backoff < kIdleBackoffMaxNs) backoff <<= 1;
         }
         __syncthreads();
         prof_add(sm, kProfIdle, pti);
@@ -1340,7 +1864,7 @@ __global__ void init_source_kernel(EngineArgs a) {
     const uint32_t units = (w + P.unit - 1) / P.unit;
     ctl->kind[0] = (P.mode == kModePlain) ? kPhPlainMult : kPhLevel;
     ctl->plevel[0] = 0;
-    ctl->nitems[0] = 0;
+    ctl->nitems[0] = 1;  // one granule per unit
     ctl->pending[0] = units;
     ctl->epoch = 0;
     ctl->desc[0] = (0ull << 32) | units;

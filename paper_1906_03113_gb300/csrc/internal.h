@@ -10,18 +10,31 @@
 
 namespace abfs {
 
-// Threads per CTA of the persistent engine.
-constexpr int kThreads = 512;
+// Threads per CTA of the persistent engine, and the CTAs per SM its register
+// budget is compiled for (512 x 2: 64 registers per thread).  The build may
+// override both (and kIlp) with -D for measurements of other shapes.
+#ifndef ABFS_THREADS
+#define ABFS_THREADS 512
+#endif
+#ifndef ABFS_MIN_CTAS
+#define ABFS_MIN_CTAS 2
+#endif
+#ifndef ABFS_ILP
+#define ABFS_ILP 4
+#endif
+constexpr int kThreads = ABFS_THREADS;
+constexpr int kMinCtas = ABFS_MIN_CTAS;
 constexpr int kWarps = kThreads / 32;
+static_assert(kThreads % 32 == 0 && kWarps <= 32, "CTA size");
 // Largest group of frontier vertices a CTA stages in shared memory at once.
 constexpr int kTileMax = 1024;
 // Entries each thread keeps in flight in the expand loop (memory-level parallelism).
-constexpr int kIlp = 4;
+constexpr int kIlp = ABFS_ILP;
 // Per-warp staging buffer for newly reached vertices.  A warp writes its
 // buffer out as one frontier block once a further expand step (32 * kIlp
 // appends) might not fit; at the end of a unit the leftovers of all warps
 // leave as one block.
-constexpr int kWarpBuf = 256;
+constexpr int kWarpBuf = 64 * kIlp < 256 ? 256 : 64 * kIlp;
 constexpr int kWarpFlushAt = kWarpBuf - 32 * kIlp;
 // Largest work unit (entry slots) and the per-unit start bitmap it needs.
 constexpr uint32_t kUnitMax = 16384;
@@ -44,6 +57,8 @@ enum PhaseKind : uint32_t {
     kPhPlainMask = 2,  // comparator: apply the visited mask to the touched rows
     kPhShrink = 3,     // physical shrink of the unvisited columns
     kPhInit = 4,       // serving: clear the outputs and bitmaps of a newly started search
+    kPhLevelScan = 5,  // submatrix method, large level: mask, multiply and claim by reductions
+    kPhExtract = 6,    // the vertices a kPhLevelScan level reached, read off the bitmaps
 };
 
 enum InstStatus : uint32_t { kIdle = 0, kRunning = 1, kDone = 2, kFailed = 3 };
@@ -129,6 +144,8 @@ struct EngineParams {
     uint32_t unit;                 // column entries per work unit
     uint32_t narrow_max;
     uint32_t narrow_edges;
+    uint32_t narrow_loop;          // 1: narrow levels run back to back on one CTA (resident runs)
+    uint32_t scan_min;             // wide levels with >= scan_min entry slots claim by reductions (0: never)
     float shrink_theta;
     uint32_t shrink_max;
     uint32_t shrink_tile;          // vertices per shrink unit
@@ -159,7 +176,20 @@ enum ProfSlot : int {
     kProfFlush = 5,    // writing the unit's leftovers as a block
     kProfAdvance = 6,  // advancing a search to its next phase
     kProfUnits = 7,    // units run (a count)
-    kProfSlots = 8
+    // resident narrow runs
+    kProfNLoad = 8,     // staging a chunk of the frontier list (columns, scan, starts)
+    kProfNExpand = 9,   // expanding it
+    kProfNAppend = 10,  // appending the warps' leftovers (and the comparator's mask)
+    kProfNDecide = 11,  // counters and the decision to go on
+    kProfNBlocks = 12,  // rewriting the last list as blocks
+    kProfNLevels = 13,  // levels run (a count)
+    // per warp inside the expand loop (sums over warps)
+    kProfXSetup = 14,    // locating the warp's first vertex and issuing the first row loads
+    kProfXLoop = 15,     // the whole loop over the warp's slots
+    kProfXProcess = 16,  // of which: mask, multiply and claim (waits for the loads)
+    kProfXFlush = 17,    // of which: writing staged vertices out
+    kProfXCalls = 18,    // expand calls per warp (a count)
+    kProfSlots = 19
 };
 
 // Per-search workspace layout: byte offsets of each buffer from the base.

@@ -60,6 +60,24 @@ MODES = [
     ("sub_wide_all", dict(mode=SUB, tile=256, narrow_max=0, narrow_edges=0, ctas_per_sm=1)),
     ("sub_shrink_every", dict(mode=SUB, tile=128, narrow_max=0, narrow_edges=0, shrink_theta=0.05,
                               shrink_max=20, unit_entries=1024)),
+    # narrow levels through the block bookkeeping instead of resident runs
+    ("sub_narrow_blocks", dict(mode=SUB, narrow_resident=0)),
+    ("plain_narrow_blocks", dict(mode=PLAIN, narrow_resident=0)),
+    # resident runs over whole searches: small chunks, several slot windows
+    ("sub_resident_all", dict(mode=SUB, tile=64, narrow_max=1 << 30, narrow_edges=1 << 30)),
+    ("plain_resident_all", dict(mode=PLAIN, tile=96, narrow_max=1 << 30, narrow_edges=1 << 30)),
+    # resident runs interrupted by shrinks (matrix switches inside and between runs)
+    ("sub_resident_shrink", dict(mode=SUB, tile=64, narrow_max=1 << 30, narrow_edges=1 << 30,
+                                 shrink_theta=0.05, shrink_max=20)),
+    # every wide level claims by reductions and a bitmap scan
+    ("sub_scan_all", dict(mode=SUB, tile=256, narrow_max=0, narrow_edges=0, claim_scan=1,
+                          unit_entries=512)),
+    ("sub_scan_shrink", dict(mode=SUB, narrow_max=64, narrow_edges=1024, claim_scan=1,
+                             shrink_theta=0.1, shrink_max=8)),
+    ("sub_no_scan", dict(mode=SUB, claim_scan=0)),
+    # frequent narrow <-> wide transitions
+    ("sub_resident_mixed", dict(mode=SUB, tile=128, narrow_max=300, narrow_edges=3000,
+                                unit_entries=512)),
 ]
 
 

@@ -110,3 +110,24 @@ def test_serve_queue_full_is_busy(graphs):
             assert srv.wait(t, 60000) == 0
     rep = srv.stop()
     assert rep["completed"] == sum(r is not None for r in results)
+
+
+@pytest.mark.gpu
+def test_serve_slot_reuse_under_churn():
+    """Many short searches through few slots: each slot is reused hundreds of
+    times while other CTAs still look at it, and every result still equals the
+    query run alone."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    abfs.build()
+    gs = [synth.er(3000, 4.0, seed=21), synth.grid(40, 25), synth.rgg_knn(4096, 4, seed=22),
+          synth.rmat(12, 8.0, seed=23)]
+    dev = [abfs.graph_create(g.colptr, g.rowidx, directed=g.directed) for g in gs]
+    try:
+        for trial in range(3):
+            cfg = abfs.serve_default_cfg(max_slots=4 + 4 * trial, memory_budget=1 << 30,
+                                         idle_exit_ms=20)
+            _serve_and_check(gs, dev, _queries(gs, 1500, 30 + trial), cfg, bursts=5)
+    finally:
+        for G in dev:
+            G.destroy()
