@@ -247,31 +247,44 @@ def bench_batch(args, ws, rank, local, torch, abfs, dist):
         _, _, st = abfs.run(G, s_, lv[:G.n], pv[:G.n], stream, None, stats=True)
         edges.append(_edges(st, d))
     total_edges = float(sum(edges))
-    plan = abfs.BatchPlan(qg, qs)
-    for _ in range(max(args.warmup, 3)):
-        plan.launch(stream)
-    torch.cuda.synchronize()
-    assert all(x == 0 for x in plan.status()), "batch failed"
     steps = max(1, min(args.steps, 20))
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
-    clocks = Clocks(local)
-    clocks.start()
-    time.sleep(0.3)
-    a.record(stream)
-    for _ in range(steps):
-        plan.launch(stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    batch_ms = a.elapsed_time(b) / steps
-    # the same queries, one launch each
-    a.record(stream)
-    for G, s_ in zip(qg, qs):
-        abfs.run(G, s_, lv[:G.n], pv[:G.n], stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    single_ms = a.elapsed_time(b)
+
+    def batched_vs_single(gs, ss, clocks=None):
+        plan = abfs.BatchPlan(gs, ss)
+        for _ in range(max(args.warmup, 3)):
+            plan.launch(stream)
+        torch.cuda.synchronize()
+        assert all(x == 0 for x in plan.status()), "batch failed"
+        if clocks is not None:
+            clocks.start()
+            time.sleep(0.3)
+        a.record(stream)
+        for _ in range(steps):
+            plan.launch(stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks is not None else None
+        bms = a.elapsed_time(b) / steps
+        plan.destroy()
+        # the same queries, one launch each
+        a.record(stream)
+        for G, s_ in zip(gs, ss):
+            abfs.run(G, s_, lv[:G.n], pv[:G.n], stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return bms, a.elapsed_time(b), clk
+
+    batch_ms, single_ms, clk = batched_vs_single(qg, qs, Clocks(local))
+    parts = {}
+    for name, lo, hi in (("512_graphs", 0, len(graphs)), ("rmat22_64_sources", len(graphs), len(qg))):
+        bms, sms, _ = batched_vs_single(qg[lo:hi], qs[lo:hi])
+        e = float(sum(edges[lo:hi]))
+        parts[name] = {"queries": hi - lo, "batched_ms": bms, "single_query_ms": sms,
+                       "batched_gteps": e / (bms * 1e-3) / 1e9,
+                       "single_query_gteps": e / (sms * 1e-3) / 1e9,
+                       "speedup_vs_single": sms / bms}
     nq = len(qg)
     value = total_edges / (batch_ms * 1e-3) / 1e9
     line = {
@@ -286,10 +299,9 @@ def bench_batch(args, ws, rank, local, torch, abfs, dist):
         "batched": {"ms": batch_ms, "queries_per_s": nq / (batch_ms * 1e-3), "gteps": value,
                     "single_query_ms": single_ms,
                     "single_query_gteps": total_edges / (single_ms * 1e-3) / 1e9,
-                    "speedup_vs_single": single_ms / batch_ms},
+                    "speedup_vs_single": single_ms / batch_ms, "parts": parts},
         "gpu_launches": 3 * steps, "clocks": clk,
     }
-    plan.destroy()
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -136,7 +136,7 @@ bool shrink_enabled(const abfs_params& p) {
 int check_params(const abfs_params& p) {
     if (p.mode > ABFS_MODE_PLAIN) return ABFS_ERR_INVALID_ARG;
     if (p.tile < 32 || p.tile > (uint32_t)kTileMax || p.tile % 32) return ABFS_ERR_INVALID_ARG;
-    if (p.unit_entries < 256 || p.unit_entries % 256 || p.unit_entries > kUnitMax)
+    if (p.unit_entries < 256 || p.unit_entries > kUnitMax || (p.unit_entries & (p.unit_entries - 1)))
         return ABFS_ERR_INVALID_ARG;
     if (p.ctas_per_sm < 1 || p.ctas_per_sm > 8) return ABFS_ERR_INVALID_ARG;
     if (!(p.shrink_theta >= 0.f) || p.shrink_theta > 1.f) return ABFS_ERR_INVALID_ARG;
@@ -150,6 +150,8 @@ EngineParams engine_params(const abfs_params& p) {
     e.mode = p.mode;
     e.tile = p.tile;
     e.unit = p.unit_entries;
+    e.unit_shift = 0;
+    while ((1u << e.unit_shift) < p.unit_entries) ++e.unit_shift;
     e.narrow_max = p.narrow_max;
     e.narrow_edges = p.narrow_edges;
     e.narrow_loop = p.narrow_resident;

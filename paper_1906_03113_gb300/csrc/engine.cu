@@ -301,12 +301,12 @@ __device__ __forceinline__ void warp_unit_starts(const Inst& I, InstCtl* ctl, co
                                                  uint32_t pn, uint32_t blk, uint32_t i,
                                                  unsigned long long g0, uint32_t w) {
     const uint32_t lane = threadIdx.x & 31;
-    const unsigned long long U = P.unit;
+    const unsigned long long U1 = P.unit - 1;  // a power of two
     unsigned long long uf = 0;
     uint32_t c = 0;
     if (w) {
-        uf = (g0 + U - 1) / U;
-        c = (uint32_t)((g0 + w + U - 1) / U - uf);
+        uf = (g0 + U1) >> P.unit_shift;
+        c = (uint32_t)(((g0 + w + U1) >> P.unit_shift) - uf);
     }
     const uint32_t incl = warp_incl_scan(c);
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
@@ -360,51 +360,59 @@ __device__ __forceinline__ void stage_warp(bool want, uint32_t v, Smem& sm, uint
     wc += __popc(mask);
 }
 
-// Total weight (column length + kVertexSlots, matrix mat_next) of this warp's
-// n staged vertices.  Whole warp; the columns are looked up again when the
-// vertices are written, so the staging buffer holds vertex ids only.
-__device__ __forceinline__ uint32_t warp_weight(Smem& sm, const Inst& I, uint32_t mat_next,
-                                                uint32_t n) {
+// Columns (matrix mat_next) of this warp's n staged vertices, lane-strided:
+// entry it of a lane is staged vertex it*32 + lane.
+constexpr int kWarpSpans = kWarpBuf / 32;
+struct WarpCols {
+    uint32_t beg[kWarpSpans];
+    uint32_t len[kWarpSpans];
+};
+
+// Looks the columns up once; returns the staged vertices' total weight
+// (column length + kVertexSlots each).  Whole warp.
+__device__ __forceinline__ uint32_t warp_cols(Smem& sm, const Inst& I, uint32_t mat_next, uint32_t n,
+                                              WarpCols& c) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t* wv = sm.wv[threadIdx.x >> 5];
     uint32_t sum = 0;
 #pragma unroll
-    for (int it = 0; it < kWarpBuf / 32; ++it) {
+    for (int it = 0; it < kWarpSpans; ++it) {
         const uint32_t i = it * 32 + lane;
-        if (i < n) sum += col_of(I, mat_next, wv[i]).len + kVertexSlots;
+        c.beg[it] = 0;
+        c.len[it] = 0;
+        if (i < n) {
+            const ColRef r = col_of(I, mat_next, wv[i]);
+            c.beg[it] = r.beg;
+            c.len[it] = r.len;
+            sum += r.len + kVertexSlots;
+        }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, d);
     return sum;
 }
 
-// Writes this warp's n staged vertices at fq[vb + voff ..] of block blk (entry
-// base eb), the group starting at weight offset woff within the block.
-// Whole warp.
+// Writes this warp's n staged vertices (columns c) at fq[vb + voff ..] of
+// block blk (entry base eb), the group starting at weight offset woff within
+// the block.  Whole warp.
 __device__ __forceinline__ void warp_emit(Smem& sm, const Inst& I, InstCtl* ctl,
-                                          const EngineParams& P, uint32_t pn, uint32_t mat_next,
+                                          const EngineParams& P, uint32_t pn, const WarpCols& c,
                                           uint32_t n, uint32_t blk, unsigned long long eb,
                                           uint32_t vb, uint32_t voff, uint32_t woff) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t* wv = sm.wv[threadIdx.x >> 5];
     uint32_t carry = woff;
-    for (uint32_t base = 0; base < n; base += 32) {
-        const uint32_t i = base + lane;
-        ColRef c;
-        c.beg = 0;
-        c.len = 0;
-        uint32_t v = 0;
-        if (i < n) {
-            v = wv[i];
-            c = col_of(I, mat_next, v);
-        }
-        const uint32_t w = i < n ? c.len + kVertexSlots : 0u;
+#pragma unroll
+    for (int it = 0; it < kWarpSpans; ++it) {
+        if ((uint32_t)it * 32 >= n) break;
+        const uint32_t i = it * 32 + lane;
+        const uint32_t w = i < n ? c.len[it] + kVertexSlots : 0u;
         const uint32_t incl = warp_incl_scan(w);
         const uint32_t pre = carry + incl - w;
         if (i < n) {
             const uint32_t at = vb + voff + i;
-            I.fq[pn][at] = v;
-            I.fbeg[pn][at] = c.beg;
+            I.fq[pn][at] = wv[i];
+            I.fbeg[pn][at] = c.beg[it];
             I.fpre[pn][at] = pre;
         }
         warp_unit_starts(I, ctl, P, pn, blk, voff + i, eb + pre, w);
@@ -414,10 +422,12 @@ __device__ __forceinline__ void warp_emit(Smem& sm, const Inst& I, InstCtl* ctl,
 }
 
 // A warp writes its staging buffer out as a frontier block of its own.
-__device__ ABFS_NOINLINE void warp_flush(Smem& sm, const Inst& I, InstCtl* ctl, const EngineParams& P,
-                           uint32_t pn, uint32_t mat_next, uint32_t& wc) {
+__device__ ABFS_NOINLINE void warp_flush(Smem& sm, const Inst& I, InstCtl* ctl,
+                                         const EngineParams& P, uint32_t pn, uint32_t mat_next,
+                                         uint32_t& wc) {
     const uint32_t n = wc;
-    const uint32_t wtot = warp_weight(sm, I, mat_next, n);
+    WarpCols c;
+    const uint32_t wtot = warp_cols(sm, I, mat_next, n, c);
     uint32_t blk = 0, vb = 0, ok = 0;
     unsigned long long eb = 0;
     if ((threadIdx.x & 31) == 0) ok = reserve_block(I, ctl, pn, n, wtot, blk, eb, vb);
@@ -425,18 +435,19 @@ __device__ ABFS_NOINLINE void warp_flush(Smem& sm, const Inst& I, InstCtl* ctl, 
     blk = __shfl_sync(0xFFFFFFFFu, blk, 0);
     vb = __shfl_sync(0xFFFFFFFFu, vb, 0);
     eb = __shfl_sync(0xFFFFFFFFu, eb, 0);
-    if (ok) warp_emit(sm, I, ctl, P, pn, mat_next, n, blk, eb, vb, 0u, 0u);
+    if (ok) warp_emit(sm, I, ctl, P, pn, c, n, blk, eb, vb, 0u, 0u);
     wc = 0;
 }
 
 // End of a unit: the leftovers of all warps (counts in sm.wcnt) leave as one
 // frontier block.  Whole CTA.
-__device__ ABFS_NOINLINE void cta_flush(Smem& sm, const Inst& I, InstCtl* ctl, const EngineParams& P,
-                          uint32_t pn, uint32_t mat_next) {
+__device__ ABFS_NOINLINE void cta_flush(Smem& sm, const Inst& I, InstCtl* ctl,
+                                        const EngineParams& P, uint32_t pn, uint32_t mat_next) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
     const uint32_t n = sm.wcnt[warp];
-    const uint32_t wtot = warp_weight(sm, I, mat_next, n);
+    WarpCols c;
+    const uint32_t wtot = warp_cols(sm, I, mat_next, n, c);
     if (lane == 0) {
         sm.wvoff[warp] = n;
         sm.wwoff[warp] = wtot;
@@ -462,7 +473,7 @@ __device__ ABFS_NOINLINE void cta_flush(Smem& sm, const Inst& I, InstCtl* ctl, c
     }
     __syncthreads();
     if (sm.gblk != kUnset && n)
-        warp_emit(sm, I, ctl, P, pn, mat_next, n, sm.gblk, sm.geb, sm.gbase, sm.wvoff[warp],
+        warp_emit(sm, I, ctl, P, pn, c, n, sm.gblk, sm.geb, sm.gbase, sm.wvoff[warp],
                   sm.wwoff[warp]);
     if (lane == 0) sm.wcnt[warp] = 0;
     __syncthreads();
@@ -1243,23 +1254,28 @@ __device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const
 }
 
 // Rewrites the list of parity pn (fn vertices; fpre holds column lengths) as
-// frontier blocks of up to kThreads*8 vertices: slot offsets within the block,
-// unit starts, and the parity's counters.  Whole CTA.
-__device__ ABFS_NOINLINE void narrow_to_blocks(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                                 uint32_t pn, uint32_t fn) {
-    constexpr uint32_t kItems = 8;
-    constexpr uint32_t kChunk = kThreads * kItems;
+// frontier blocks of up to kWarps*kWarpBuf vertices: slot offsets within the
+// block, unit starts, and the parity's counters.  The warp staging buffers
+// (empty here) stage each chunk so global reads and writes stay coalesced.
+// Whole CTA.
+__device__ ABFS_NOINLINE void narrow_to_blocks(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                               Smem& sm, uint32_t pn, uint32_t fn) {
+    constexpr uint32_t kChunk = kWarps * kWarpBuf;
+    constexpr uint32_t kItems = kChunk / kThreads;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t* buf = &sm.wv[0][0];
     unsigned long long eb = 0;
     uint32_t nb = 0;
     for (uint32_t c0 = 0; c0 < fn; c0 += kChunk, ++nb) {
         const uint32_t cnt = min(kChunk, fn - c0);
+        for (uint32_t i = tid; i < cnt; i += kThreads) buf[i] = ld_l2(I.fpre[pn] + c0 + i);
+        __syncthreads();
         uint32_t x[kItems];
         uint32_t sum = 0;
 #pragma unroll
         for (uint32_t q = 0; q < kItems; ++q) {
             const uint32_t idx = tid * kItems + q;
-            x[q] = idx < cnt ? ld_l2(I.fpre[pn] + c0 + idx) + kVertexSlots : 0u;
+            x[q] = idx < cnt ? buf[idx] + kVertexSlots : 0u;
             sum += x[q];
         }
         const uint32_t incl = warp_incl_scan(sum);
@@ -1277,10 +1293,13 @@ __device__ ABFS_NOINLINE void narrow_to_blocks(const Inst& I, InstCtl* ctl, cons
         const bool ok = nb < I.bcap && nb < kBlockMask;
         for (uint32_t q = 0; q < kItems; ++q) {
             const uint32_t idx = tid * kItems + q;
-            if (idx < cnt && ok) I.fpre[pn][c0 + idx] = run;
+            if (idx < cnt) buf[idx] = run;
             warp_unit_starts(I, ctl, P, pn, nb, idx, eb + run, (idx < cnt && ok) ? x[q] : 0u);
             run += x[q];
         }
+        __syncthreads();
+        if (ok)
+            for (uint32_t i = tid; i < cnt; i += kThreads) I.fpre[pn][c0 + i] = buf[i];
         if (tid == 0) {
             if (ok) {
                 Block* B = I.blk[pn] + nb;
@@ -1292,7 +1311,7 @@ __device__ ABFS_NOINLINE void narrow_to_blocks(const Inst& I, InstCtl* ctl, cons
             }
         }
         eb += total;
-        __syncthreads();  // warp_sums is reused
+        __syncthreads();  // buf and warp_sums are reused
     }
     if (tid == 0) {
         st_relaxed64(&ctl->bctr[pn], (eb << kBlockBits) | (unsigned long long)nb);
@@ -1601,26 +1620,43 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
     }
 }
 
+// Control block of instance q (fixed for the launch, also per serving slot,
+// but a serving slot's other descriptor fields change while the launch runs,
+// so those launches read it without the read-only path).
+__device__ __forceinline__ InstCtl* ctl_of(const EngineArgs& a, uint32_t q) {
+    const unsigned long long* p = reinterpret_cast<const unsigned long long*>(&a.insts[q].ctl);
+    return reinterpret_cast<InstCtl*>(a.serve ? ld_relaxed64(p) : __ldg(p));
+}
+
 // Whether instance q has an untaken unit in its published phase (or, when
-// serving, is a newly submitted search waiting to start).
-__device__ __forceinline__ bool has_work(const EngineArgs& a, uint32_t q) {
+// serving, is a newly submitted search waiting to start).  The published
+// phase's grab epoch and descriptor are returned in e and d.
+__device__ __forceinline__ bool has_work(const EngineArgs& a, uint32_t q, uint32_t& e,
+                                         unsigned long long& d) {
     if (a.serve) {
         // a slot that never held a search has no control block yet
         const uint32_t st = ld_relaxed(a.slot_state + q);
         if (st == kSlotSubmitted) return true;
         if (st != kSlotRunning) return false;
     }
-    InstCtl* ctl = a.insts[q].ctl;
-    if (ld_relaxed(&ctl->status) != kRunning) return false;
+    const InstCtl* ctl = ctl_of(a, q);
+    // one round of independent loads
+    const uint32_t status = ld_relaxed(&ctl->status);
     const unsigned long long g = ld_relaxed64(&ctl->grab);
-    const uint32_t e = (uint32_t)(g >> 32), taken = (uint32_t)g;
-    const unsigned long long d = ld_relaxed64(&ctl->desc[e & 1]);
-    return (uint32_t)(d >> 32) == e && taken < (uint32_t)d;
+    const unsigned long long d0 = ld_relaxed64(&ctl->desc[0]);
+    const unsigned long long d1 = ld_relaxed64(&ctl->desc[1]);
+    e = (uint32_t)(g >> 32);
+    d = (e & 1) ? d1 : d0;
+    const uint32_t taken = (uint32_t)g;
+    return status == kRunning && (uint32_t)(d >> 32) == e && taken < (uint32_t)d;
 }
 
 // One lane: takes a unit of instance q if one is left (or claims the start
-// of a submitted search); fills sm.cmd.
-__device__ __forceinline__ bool take_unit(const EngineArgs& a, uint32_t q, Smem& sm) {
+// of a submitted search); fills sm.cmd.  (e_seen, d_seen) is what has_work
+// saw: the descriptor of epoch e_seen, reused when the grab lands in that
+// epoch.
+__device__ __forceinline__ bool take_unit(const EngineArgs& a, uint32_t q, Smem& sm, uint32_t e_seen,
+                                          unsigned long long d_seen) {
     if (a.serve && ld_relaxed(a.slot_state + q) == kSlotSubmitted) {
         if (atomicCAS(a.slot_state + q, (uint32_t)kSlotSubmitted, (uint32_t)kSlotRunning) !=
             kSlotSubmitted)
@@ -1630,10 +1666,12 @@ __device__ __forceinline__ bool take_unit(const EngineArgs& a, uint32_t q, Smem&
         sm.cmd.start = 1;
         return true;
     }
-    InstCtl* ctl = a.insts[q].ctl;
+    InstCtl* ctl = ctl_of(a, q);
     const unsigned long long old = atomicAdd(&ctl->grab, 1ull);
     const uint32_t e = (uint32_t)(old >> 32), t = (uint32_t)old;
-    const unsigned long long d = ld_relaxed64(&ctl->desc[e & 1]);
+    // the descriptor of epoch e is written before grab moves to e
+    const unsigned long long d =
+        (e == e_seen && (uint32_t)(d_seen >> 32) == e) ? d_seen : ld_relaxed64(&ctl->desc[e & 1]);
     if ((uint32_t)(d >> 32) != e || t >= (uint32_t)d) return false;
     __threadfence();  // acquire: the phase fields and the data of earlier phases
     const uint32_t qq = e & 1;
@@ -1695,12 +1733,14 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
         for (uint32_t base = 0; base < a.ninst && !got; base += 32) {
             const uint32_t idx = base + lane;
             const uint32_t q = (cursor + idx) % a.ninst;
-            const bool avail = idx < a.ninst && has_work(a, q);
+            uint32_t e_seen = 0;
+            unsigned long long d_seen = 0;
+            const bool avail = idx < a.ninst && has_work(a, q, e_seen, d_seen);
             uint32_t mask = __ballot_sync(0xFFFFFFFFu, avail);
             while (mask && !got) {
                 const uint32_t l = __ffs(mask) - 1;
                 bool ok = false;
-                if (lane == l) ok = take_unit(a, q, sm);
+                if (lane == l) ok = take_unit(a, q, sm, e_seen, d_seen);
                 got = __shfl_sync(0xFFFFFFFFu, ok, l);
                 mask &= mask - 1;
             }

@@ -141,7 +141,8 @@ struct Inst {
 struct EngineParams {
     uint32_t mode;
     uint32_t tile;                 // vertices per staged group / touched rows per mask unit
-    uint32_t unit;                 // column entries per work unit
+    uint32_t unit;                 // granule of work units in entry slots (a power of two)
+    uint32_t unit_shift;           // log2(unit)
     uint32_t narrow_max;
     uint32_t narrow_edges;
     uint32_t narrow_loop;          // 1: narrow levels run back to back on one CTA (resident runs)
