@@ -251,8 +251,11 @@ def bench_batch(args, ws, rank, local, torch, abfs, dist):
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
 
+    # parameters for the whole batch from the batch autotuner (outside the timing)
+    tuned, tuned_ms = abfs.batch_tune(qg, qs)
+
     def batched_vs_single(gs, ss, clocks=None):
-        plan = abfs.BatchPlan(gs, ss)
+        plan = abfs.BatchPlan(gs, ss, params=tuned)
         for _ in range(max(args.warmup, 3)):
             plan.launch(stream)
         torch.cuda.synchronize()
@@ -294,12 +297,14 @@ def bench_batch(args, ws, rank, local, torch, abfs, dist):
         "config": {"workload": "batch512_rmat22x64",
                    "graph": "512 ER/R-MAT graphs, n log-uniform in [2^10, 2^18], avg degree "
                             "U[4,32] (seed 1), plus 64 sources on R-MAT-22 (seed 2)",
-                   "queries": nq, "step": "one persistent launch (CUDA graph replay) of all queries",
+                   "queries": nq, "step": "one persistent launch (CUDA graph replay) of all queries, "
+                            "parameters from the batch autotuner",
                    "l2": "inputs larger than L2 (R-MAT-22 rowidx 513 MB, 576 workspaces)"},
         "batched": {"ms": batch_ms, "queries_per_s": nq / (batch_ms * 1e-3), "gteps": value,
                     "single_query_ms": single_ms,
                     "single_query_gteps": total_edges / (single_ms * 1e-3) / 1e9,
-                    "speedup_vs_single": single_ms / batch_ms, "parts": parts},
+                    "speedup_vs_single": single_ms / batch_ms, "parts": parts,
+                    "tuned_params": tuned.as_dict(), "tuner_ms": tuned_ms},
         "gpu_launches": 3 * steps, "clocks": clk,
     }
     if rank == 0:

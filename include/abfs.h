@@ -223,6 +223,21 @@ int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count, uint32_t 
               const char* cache_path, abfs_stream_t stream, abfs_params* best, float* best_ms);
 
 /*
+ * Batch autotuner: for each candidate parameter set (work granule, narrow
+ * bounds, reduction claims, shrink threshold) builds a batch plan over the
+ * `count` searches (graph g[i], source sources[i]), replays it after one
+ * warm-up and keeps the fastest whole-batch time; *best receives that set
+ * and *best_ms its mean ms per launch.  Device memory for the trial plans and
+ * their outputs is allocated and freed inside.  With `cache_path` (JSON
+ * lines), an earlier choice for the same GPU, SM count, mode and batch size
+ * class is returned without measuring, and a new choice is appended.
+ * Synchronises `stream`.
+ */
+int abfs_batch_tune(const abfs_graph_t* g, const uint32_t* sources, uint32_t count, uint32_t mode,
+                    const char* cache_path, abfs_stream_t stream, abfs_params* best,
+                    float* best_ms);
+
+/*
  * Serving: a long-lived device loop answers BFS queries on resident graphs
  * (continuous batching).  Requests are queued by abfs_serve_submit; a host
  * admission thread moves them into free device slots as soon as a slot and

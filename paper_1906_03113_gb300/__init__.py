@@ -9,6 +9,7 @@ from .binding import (  # noqa: F401
     MODE_SUBMATRIX,
     AbfsError,
     BatchPlan,
+    batch_tune,
     Graph,
     Server,
     ServeCfg,

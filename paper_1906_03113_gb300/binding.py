@@ -151,6 +151,8 @@ def load():
         "abfs_batch_destroy": ([vp], c_int),
         "abfs_tune": ([vp, P(u32), u32, u32, ctypes.c_char_p, vp, P(Params),
                        P(ctypes.c_float)], c_int),
+        "abfs_batch_tune": ([P(vp), P(u32), u32, u32, ctypes.c_char_p, vp, P(Params),
+                             P(ctypes.c_float)], c_int),
         "abfs_set_allocator": ([vp, vp, vp], c_int),
         "abfs_run_static": ([vp, vp, u32, u64, u32, vp, vp, vp], c_int),
         "abfs_serve_default_cfg": ([P(ServeCfg)], c_int),
@@ -489,4 +491,18 @@ def tune(g: Graph, sources, mode: int = MODE_SUBMATRIX, cache_path: str | None =
                           cache_path.encode() if cache_path else None, _stream_ptr(stream),
                           ctypes.byref(best), ctypes.byref(ms))
     _check(rc, "abfs_tune")
+    return best, float(ms.value)
+
+
+def batch_tune(graphs: list[Graph], sources, mode: int = MODE_SUBMATRIX,
+               cache_path: str | None = None, stream=None):
+    """abfs_batch_tune: (best Params for the whole batch, mean ms per launch)."""
+    count = len(graphs)
+    src = (ctypes.c_uint32 * count)(*[int(s) for s in sources])
+    best = Params()
+    ms = ctypes.c_float()
+    rc = load().abfs_batch_tune(_ptr_array([g.handle.value for g in graphs]), src, count, mode,
+                                cache_path.encode() if cache_path else None, _stream_ptr(stream),
+                                ctypes.byref(best), ctypes.byref(ms))
+    _check(rc, "abfs_batch_tune")
     return best, float(ms.value)

@@ -967,3 +967,146 @@ extern "C" int abfs_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)
 }
 
 extern "C" const char* abfs_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// batch autotuner
+// ---------------------------------------------------------------------------
+
+namespace {
+
+std::string batch_class(const abfs_graph_t* g, uint32_t count) {
+    double n = 0, nnz = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        n += g[i]->n;
+        nnz += (double)g[i]->nnz;
+    }
+    std::ostringstream o;
+    o << "batch" << count << "_n2^" << (int)std::ceil(std::log2(n + 1)) << "_e2^"
+      << (int)std::ceil(std::log2(nnz + 1));
+    return o.str();
+}
+
+}  // namespace
+
+extern "C" int abfs_batch_tune(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
+                               uint32_t mode, const char* cache_path, abfs_stream_t stream,
+                               abfs_params* best, float* best_ms) {
+    if (!g || !sources || count == 0 || mode > ABFS_MODE_PLAIN) return ABFS_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < count; ++i)
+        if (!g[i] || sources[i] >= g[i]->n) return ABFS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const std::string key_gpu = gpu_name(g[0]->device);
+    const std::string key_cls = batch_class(g, count);
+    if (cache_path) {
+        std::ifstream in(cache_path);
+        std::string line, found;
+        while (std::getline(in, line)) {
+            std::string gpu, cls;
+            double sms = 0, md = -1;
+            if (json_str(line, "gpu", &gpu) && json_str(line, "class", &cls) &&
+                json_num(line, "sms", &sms) && json_num(line, "mode", &md) && gpu == key_gpu &&
+                cls == key_cls && (int)sms == g[0]->sms && (uint32_t)md == mode)
+                found = line;
+        }
+        if (!found.empty()) {
+            abfs_params p = default_params();
+            double v;
+            if (json_num(found, "tile", &v)) p.tile = (uint32_t)v;
+            if (json_num(found, "unit_entries", &v)) p.unit_entries = (uint32_t)v;
+            if (json_num(found, "narrow_max", &v)) p.narrow_max = (uint32_t)v;
+            if (json_num(found, "narrow_edges", &v)) p.narrow_edges = (uint32_t)v;
+            if (json_num(found, "ctas_per_sm", &v)) p.ctas_per_sm = (uint32_t)v;
+            if (json_num(found, "shrink_theta", &v)) p.shrink_theta = (float)v;
+            if (json_num(found, "shrink_max", &v)) p.shrink_max = (uint32_t)v;
+            if (json_num(found, "narrow_resident", &v)) p.narrow_resident = (uint32_t)v;
+            if (json_num(found, "claim_scan", &v)) p.claim_scan = (uint32_t)v;
+            p.mode = mode;
+            if (check_params(p) == ABFS_OK) {
+                if (best) *best = p;
+                if (best_ms && json_num(found, "ms", &v)) *best_ms = (float)v;
+                return ABFS_OK;
+            }
+        }
+    }
+    // candidates: granule x narrow bounds (x reduction claims), plus shrink thresholds
+    std::vector<abfs_params> cands;
+    const uint32_t granules[] = {512, 1024, 4096};
+    const uint32_t narrow_e[] = {16384, 65536};
+    const uint32_t scans[] = {0, 1u << 22};
+    for (uint32_t ue : granules)
+        for (uint32_t ne : narrow_e)
+            for (uint32_t sc : scans) {
+                if (mode == ABFS_MODE_PLAIN && sc) continue;
+                abfs_params p = default_params();
+                p.mode = mode;
+                p.unit_entries = ue;
+                p.narrow_edges = ne;
+                p.narrow_max = ne / 16;
+                p.claim_scan = sc;
+                cands.push_back(p);
+            }
+    if (mode == ABFS_MODE_SUBMATRIX) {
+        const float thetas[] = {0.5f, 0.8f};
+        for (float th : thetas) {
+            abfs_params p = default_params();
+            p.shrink_theta = th;
+            p.shrink_max = 1;
+            cands.push_back(p);
+        }
+    }
+    // outputs for the trial plans
+    std::vector<int32_t*> lv(count, nullptr), pr(count, nullptr);
+    int rc = ABFS_OK;
+    for (uint32_t i = 0; i < count && !rc; ++i) {
+        rc = dev_alloc((void**)&lv[i], (size_t)g[i]->n * 4);
+        if (!rc) rc = dev_alloc((void**)&pr[i], (size_t)g[i]->n * 4);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = ABFS_ERR_CUDA;
+    float best_time = INFINITY;
+    abfs_params best_p = default_params();
+    best_p.mode = mode;
+    std::vector<int32_t> st(count);
+    for (size_t ci = 0; ci < cands.size() && !rc; ++ci) {
+        abfs_batch_t b = nullptr;
+        rc = abfs_batch_create(g, sources, count, lv.data(), pr.data(), &cands[ci], stream, &b);
+        if (rc) break;
+        const int reps = 2;
+        rc = abfs_batch_launch(b, stream);  // warm-up
+        if (!rc && cudaEventRecord(e0, s) != cudaSuccess) rc = ABFS_ERR_CUDA;
+        for (int r = 0; r < reps && !rc; ++r) rc = abfs_batch_launch(b, stream);
+        if (!rc && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            rc = ABFS_ERR_CUDA;
+        if (!rc) rc = abfs_batch_status(b, stream, st.data());
+        bool ok = !rc;
+        for (uint32_t i = 0; i < count && ok; ++i) ok = st[i] == ABFS_OK;
+        float ms = 0;
+        if (ok) {
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (ms < best_time) {
+                best_time = ms;
+                best_p = cands[ci];
+            }
+        }
+        const int rd = abfs_batch_destroy(b);
+        if (!rc) rc = rd;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (uint32_t i = 0; i < count; ++i) {
+        dev_free(lv[i]);
+        dev_free(pr[i]);
+    }
+    if (rc) return rc;
+    if (!(best_time < INFINITY)) return ABFS_ERR_DEVICE;
+    if (best) *best = best_p;
+    if (best_ms) *best_ms = best_time;
+    if (cache_path) {
+        std::ofstream o(cache_path, std::ios::app);
+        o << "{\"gpu\":\"" << key_gpu << "\",\"sms\":" << g[0]->sms << ",\"class\":\"" << key_cls
+          << "\"," << params_json(best_p) << ",\"ms\":" << best_time << "}\n";
+    }
+    return ABFS_OK;
+}

@@ -267,6 +267,24 @@ def test_tune_keeps_results(small, tmp_path):
     _check(g, srcs[0], level, parent, "tuned")
 
 
+def test_batch_tune_picks_a_valid_set(small, tmp_path):
+    gs, dev = small
+    names = ["er_2000", "rmat_14", "grid_100x37", "rgg_2_15"]
+    graphs = [dev[n] for n in names]
+    srcs = [_sources(gs[n])[0] for n in names]
+    cache = str(tmp_path / "batch_tune.json")
+    best, ms = abfs.batch_tune(graphs, srcs, SUB, cache)
+    assert ms > 0 and best.unit_entries in (512, 1024, 4096)
+    best2, _ = abfs.batch_tune(graphs, srcs, SUB, cache)   # from the cache
+    assert best2.as_dict() == best.as_dict()
+    plan = abfs.BatchPlan(graphs, srcs, params=best)
+    plan.launch()
+    assert plan.status() == [0] * len(names)
+    for n, s, L, P in zip(names, srcs, plan.levels, plan.parents):
+        _check(gs[n], s, L, P, f"tuned batch {n}")
+    plan.destroy()
+
+
 def test_device_inputs_and_validation():
     g = synth.rmat(12, 8.0, seed=5)
     cp = torch.from_numpy(g.colptr.view(np.int32)).cuda()
