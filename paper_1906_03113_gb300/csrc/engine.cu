@@ -421,21 +421,56 @@ __device__ __forceinline__ void warp_emit(Smem& sm, const Inst& I, InstCtl* ctl,
     __syncwarp();
 }
 
-// A warp writes its staging buffer out as a frontier block of its own.
-__device__ ABFS_NOINLINE void warp_flush(Smem& sm, const Inst& I, InstCtl* ctl,
-                                         const EngineParams& P, uint32_t pn, uint32_t mat_next,
-                                         uint32_t& wc) {
+// A warp writes its staging buffer out as a frontier block of its own.  It is
+// called from inside the expand loop, so it keeps little state: the columns are
+// looked up once for the block's weight and again while writing (a cached copy
+// would cost the loop registers).
+#ifdef ABFS_FLUSH_INLINE
+__device__ __forceinline__ void warp_flush(
+#else
+__device__ ABFS_NOINLINE void warp_flush(
+#endif
+    Smem& sm, const Inst& I, InstCtl* ctl, const EngineParams& P, uint32_t pn, uint32_t mat_next,
+    uint32_t& wc) {
+    const uint32_t lane = threadIdx.x & 31;
     const uint32_t n = wc;
-    WarpCols c;
-    const uint32_t wtot = warp_cols(sm, I, mat_next, n, c);
+    const uint32_t* wv = sm.wv[threadIdx.x >> 5];
+    uint32_t wtot = 0;
+    for (uint32_t i = lane; i < n; i += 32) wtot += col_of(I, mat_next, wv[i]).len + kVertexSlots;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) wtot += __shfl_xor_sync(0xFFFFFFFFu, wtot, d);
     uint32_t blk = 0, vb = 0, ok = 0;
     unsigned long long eb = 0;
-    if ((threadIdx.x & 31) == 0) ok = reserve_block(I, ctl, pn, n, wtot, blk, eb, vb);
+    if (lane == 0) ok = reserve_block(I, ctl, pn, n, wtot, blk, eb, vb);
     ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
     blk = __shfl_sync(0xFFFFFFFFu, blk, 0);
     vb = __shfl_sync(0xFFFFFFFFu, vb, 0);
     eb = __shfl_sync(0xFFFFFFFFu, eb, 0);
-    if (ok) warp_emit(sm, I, ctl, P, pn, c, n, blk, eb, vb, 0u, 0u);
+    if (ok) {
+        uint32_t carry = 0;
+        for (uint32_t base = 0; base < n; base += 32) {
+            const uint32_t i = base + lane;
+            ColRef c;
+            c.beg = 0;
+            c.len = 0;
+            uint32_t v = 0;
+            if (i < n) {
+                v = wv[i];
+                c = col_of(I, mat_next, v);
+            }
+            const uint32_t w = i < n ? c.len + kVertexSlots : 0u;
+            const uint32_t incl = warp_incl_scan(w);
+            const uint32_t pre = carry + incl - w;
+            if (i < n) {
+                I.fq[pn][vb + i] = v;
+                I.fbeg[pn][vb + i] = c.beg;
+                I.fpre[pn][vb + i] = pre;
+            }
+            warp_unit_starts(I, ctl, P, pn, blk, i, eb + pre, w);
+            carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        }
+    }
+    __syncwarp();
     wc = 0;
 }
 
@@ -573,21 +608,26 @@ enum ClaimVar : int {
                      // return; an extraction phase collects the new vertices afterwards
 };
 
+// Groups of 32 entries each thread keeps in flight, per claim variant.
+__host__ __device__ constexpr int ilp_of(int var) { return var == kVarScan ? kIlpScan : kIlp; }
+
 // Entries (r[u] in column j[u]; r[u] == kUnset: none) at level k.  Each stage issues
 // kIlp independent memory operations before consuming any.  Submatrix mode
 // appends the vertices of level k+1 to the next frontier; comparator mode
 // appends first-touched rows to the touched list.  All 32 lanes must call.
 template <int MODE, int VAR>
 __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const EngineParams& P,
-                                              Smem& sm, uint32_t k, const uint32_t (&r)[kIlp],
-                                              const uint32_t (&j)[kIlp], Tally& t, uint32_t& wc) {
+                                              Smem& sm, uint32_t k, const uint32_t (&r)[ilp_of(VAR)],
+                                              const uint32_t (&j)[ilp_of(VAR)], Tally& t,
+                                              uint32_t& wc) {
+    constexpr int L = ilp_of(VAR);
     const uint32_t p = k & 1;
     if (MODE == kModeSub) {
         const uint32_t* test_bm = I.bm[p];
         uint32_t* write_bm = I.bm[p ^ 1];
-        uint32_t w[kIlp];
+        uint32_t w[L];
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u)
+        for (int u = 0; u < L; ++u)
             w[u] = r[u] != kUnset
                        ? (VAR == kVarNarrow ? ld_l2(test_bm + (r[u] >> 5))
                                             : ld_frozen(test_bm + (r[u] >> 5)))
@@ -597,7 +637,7 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
             // least column still wins, and the new vertices are read off the
             // bitmaps once the level is complete
 #pragma unroll
-            for (int u = 0; u < kIlp; ++u) {
+            for (int u = 0; u < L; ++u) {
                 if (!((w[u] >> (r[u] & 31)) & 1u)) {
                     ++t.unmasked;
                     ++t.claims;
@@ -610,9 +650,9 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
         // rows outside V_{k+1} are masked before the multiply; the (min, index)
         // product is an atomicMin of j into parent[r], and moving parent[r]
         // off "unset" claims r for level k+1
-        bool win[kIlp];
+        bool win[L];
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
+        for (int u = 0; u < L; ++u) {
             win[u] = false;
             if (!((w[u] >> (r[u] & 31)) & 1u)) {
                 ++t.unmasked;
@@ -621,7 +661,7 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
             }
         }
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
+        for (int u = 0; u < L; ++u) {
             if (win[u]) {
                 I.level[r[u]] = (int32_t)(k + 1);
                 atomicOr(write_bm + (r[u] >> 5), 1u << (r[u] & 31));
@@ -630,9 +670,9 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
         }
     } else {
         // multiply first: every entry reaches the accumulator
-        unsigned long long old[kIlp];
+        unsigned long long old[L];
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
+        for (int u = 0; u < L; ++u) {
             old[u] = 0ull;
             if (r[u] != kUnset) {
                 ++t.unmasked;
@@ -644,12 +684,12 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
         // (narrow runs stage it with the warp's other appends)
         if (VAR == kVarNarrow) {
 #pragma unroll
-            for (int u = 0; u < kIlp; ++u)
+            for (int u = 0; u < L; ++u)
                 stage_warp(r[u] != kUnset && (uint32_t)(old[u] >> 32) != plain_stamp(k), r[u], sm, wc);
             return;
         }
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
+        for (int u = 0; u < L; ++u) {
             const bool first = r[u] != kUnset && (uint32_t)(old[u] >> 32) != plain_stamp(k);
             const uint32_t mask = __ballot_sync(0xFFFFFFFFu, first);
             if (mask) {
@@ -708,6 +748,7 @@ template <int MODE, int VAR>
 __device__ __forceinline__ void expand_core(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                              uint32_t cnt, uint32_t l0, uint32_t l1, uint32_t mat,
                              uint32_t mat_next, uint32_t k, Tally& t) {
+    constexpr int L = ilp_of(VAR);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #ifdef ABFS_EXPAND_PROFILE
     const long long xt0 = sm.prof_on ? clock64() : 0ll;
@@ -732,10 +773,10 @@ __device__ __forceinline__ void expand_core(const Inst& I, InstCtl* ctl, const E
     }
     uint32_t starts = 0;  // vertex starts in [e0, current group base)
     // row index (kUnset: no entry in this slot) and frontier column of each group
-    uint32_t r[kIlp], j[kIlp];
-    auto load_step = [&](uint32_t base, uint32_t (&rr)[kIlp], uint32_t (&jj)[kIlp]) {
+    uint32_t r[L], j[L];
+    auto load_step = [&](uint32_t base, uint32_t (&rr)[L], uint32_t (&jj)[L]) {
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
+        for (int u = 0; u < L; ++u) {
             const uint32_t gb = base + 32 * u;
             const uint32_t rel = gb - l0;
             const uint32_t sh = rel & 31;
@@ -758,19 +799,19 @@ __device__ __forceinline__ void expand_core(const Inst& I, InstCtl* ctl, const E
     long long xt1 = 0, xflush = 0, xproc = 0;
     if (sm.prof_on) xt1 = clock64();
 #endif
-    for (uint32_t base = e0; base < e1; base += 32 * kIlp) {
-        uint32_t r2[kIlp], j2[kIlp];
-        if (base + 32 * kIlp < e1) {
-            load_step(base + 32 * kIlp, r2, j2);
+    for (uint32_t base = e0; base < e1; base += 32 * L) {
+        uint32_t r2[L], j2[L];
+        if (base + 32 * L < e1) {
+            load_step(base + 32 * L, r2, j2);
         } else {
 #pragma unroll
-            for (int u = 0; u < kIlp; ++u) {
+            for (int u = 0; u < L; ++u) {
                 r2[u] = kUnset;
                 j2[u] = 0;
             }
         }
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) t.read += (r[u] != kUnset);
+        for (int u = 0; u < L; ++u) t.read += (r[u] != kUnset);
 #ifdef ABFS_EXPAND_PROFILE
         const long long xp0 = sm.prof_on ? clock64() : 0ll;
 #endif
@@ -793,7 +834,7 @@ __device__ __forceinline__ void expand_core(const Inst& I, InstCtl* ctl, const E
         if (sm.prof_on) xflush += clock64() - xp1;
 #endif
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
+        for (int u = 0; u < L; ++u) {
             r[u] = r2[u];
             j[u] = j2[u];
         }

@@ -30,6 +30,12 @@ static_assert(kThreads % 32 == 0 && kWarps <= 32, "CTA size");
 constexpr int kTileMax = 1024;
 // Entries each thread keeps in flight in the expand loop (memory-level parallelism).
 constexpr int kIlp = ABFS_ILP;
+// Entries in flight per thread in levels that claim by reductions (nothing is
+// staged there, so the registers go to more loads in flight).
+#ifndef ABFS_ILP_SCAN
+#define ABFS_ILP_SCAN 4
+#endif
+constexpr int kIlpScan = ABFS_ILP_SCAN;
 // Per-warp staging buffer for newly reached vertices.  A warp writes its
 // buffer out as one frontier block once a further expand step (32 * kIlp
 // appends) might not fit; at the end of a unit the leftovers of all warps
@@ -37,7 +43,11 @@ constexpr int kIlp = ABFS_ILP;
 constexpr int kWarpBuf = 64 * kIlp < 256 ? 256 : 64 * kIlp;
 constexpr int kWarpFlushAt = kWarpBuf - 32 * kIlp;
 // Largest work unit (entry slots) and the per-unit start bitmap it needs.
-constexpr uint32_t kUnitMax = 16384;
+#ifndef ABFS_UNIT_MAX
+#define ABFS_UNIT_MAX 32768
+#endif
+constexpr uint32_t kUnitMax = ABFS_UNIT_MAX;
+static_assert((kUnitMax & (kUnitMax - 1)) == 0 && kUnitMax >= 1024, "unit size");
 constexpr int kStartWords = kUnitMax / 32 + 2;
 // Marker of an unset parent / unclaimed vertex (reads as -1 through int32).
 constexpr uint32_t kUnset = 0xFFFFFFFFu;
