@@ -1383,7 +1383,9 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
     __syncthreads();
     const uint32_t sw = sm.nr_sw, mat_cur = sm.nr_mcur, mat_prev = sm.nr_mprev;
     bool lens = false;
-    for (;;) {
+    // a search has at most n levels: a broken invariant ends the run instead
+    // of looping
+    for (uint32_t guard = I.n + 1;; --guard) {
         const uint32_t pn = (k + 1) & 1;
         const uint32_t f = sm.nr_f;
         const uint32_t mat = k >= sw ? mat_cur : mat_prev;
@@ -1441,7 +1443,7 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
             sm.nt_cnt = 0;
             sm.nq_slots = 0;
             uint32_t stop = 0;
-            if (fn == 0 || err != 0 || fn > P.narrow_max || slots > P.narrow_edges)
+            if (fn == 0 || err != 0 || fn > P.narrow_max || slots > P.narrow_edges || guard <= 1)
                 stop = 1;
             else if (MODE == kModeSub && shrink_due(P, sm.nr_reached + fn, I.n, sm.nr_shrinks))
                 stop = 1;
