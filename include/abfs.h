@@ -120,6 +120,10 @@ int abfs_version(void);
 /* Fills *p with defaults (submatrix mode, no shrink). */
 int abfs_default_params(abfs_params* p);
 
+/* ABFS_OK if *p is a valid parameter set, else ABFS_ERR_INVALID_ARG (the same
+ * check every call that takes parameters makes).  Needs no device. */
+int abfs_check_params(const abfs_params* p);
+
 /*
  * Creates a device-resident graph from CSC arrays (Section 9's compressed
  * format, applied to A^T).  The arrays are copied: the caller keeps ownership

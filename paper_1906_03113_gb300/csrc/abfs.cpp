@@ -444,6 +444,11 @@ extern "C" int abfs_default_params(abfs_params* p) {
     return ABFS_OK;
 }
 
+extern "C" int abfs_check_params(const abfs_params* p) {
+    if (!p) return ABFS_ERR_INVALID_ARG;
+    return check_params(*p);
+}
+
 extern "C" int abfs_graph_create(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n,
                                  uint64_t nnz, int directed, uint32_t flags, abfs_stream_t stream,
                                  abfs_graph_t* out) {

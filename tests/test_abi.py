@@ -31,8 +31,9 @@ def test_default_params_are_valid(lib):
     p = abfs.default_params()
     assert p.mode == abfs.MODE_SUBMATRIX
     assert 32 <= p.tile <= 1024 and p.tile % 32 == 0
-    assert p.unit_entries >= 256 and p.unit_entries % 256 == 0
+    assert p.unit_entries >= 256 and p.unit_entries & (p.unit_entries - 1) == 0
     assert p.timeout_ms > 0
+    assert lib.abfs_check_params(ctypes.byref(p)) == 0
 
 
 def test_invalid_arguments_are_rejected_before_any_device_work(lib):
@@ -69,3 +70,19 @@ def test_parameter_validation(lib):
                                 "ctas_per_sm", "shrink_theta", "shrink_max", "timeout_ms"}
     # footprint of a null graph is an argument error, not a crash
     assert lib.abfs_graph_footprint(None, ctypes.byref(p), ctypes.byref(size)) == binding.ERR_INVALID_ARG
+    assert lib.abfs_check_params(None) == binding.ERR_INVALID_ARG
+
+    def check(**kw):
+        return lib.abfs_check_params(ctypes.byref(abfs.default_params(**kw)))
+
+    ok, bad = 0, binding.ERR_INVALID_ARG
+    for kw in (dict(tile=32), dict(tile=1024), dict(unit_entries=256), dict(unit_entries=32768),
+               dict(mode=abfs.MODE_PLAIN), dict(ctas_per_sm=1), dict(shrink_theta=0.5, shrink_max=2),
+               dict(narrow_resident=0), dict(claim_scan=0), dict(claim_scan=1),
+               dict(narrow_max=0, narrow_edges=0)):
+        assert check(**kw) == ok, kw
+    for kw in (dict(tile=16), dict(tile=1056), dict(tile=100), dict(unit_entries=128),
+               dict(unit_entries=768), dict(unit_entries=65536), dict(mode=2), dict(ctas_per_sm=0),
+               dict(ctas_per_sm=9), dict(shrink_theta=-0.1), dict(shrink_theta=1.5),
+               dict(timeout_ms=0), dict(narrow_resident=2)):
+        assert check(**kw) == bad, kw
