@@ -148,6 +148,8 @@ struct Smem {
     uint32_t warp_sums[kWarps + 1];
     // walk state of the current unit
     uint32_t cur_b, cur_i, abort_unit, sub_cnt, sub_nseg;
+    // first staged vertex of each warp's slots (the expand loop's vb), kNoVb: none
+    uint32_t wvb[kWarps];
     unsigned long long sub_g0, sub_end;
     uint32_t seg_idx[32], seg_pos[32];
     unsigned long long seg_eb[32];
@@ -736,6 +738,26 @@ __device__ __forceinline__ void stats_flush(Smem& sm, InstCtl* ctl) {
 // work units
 // ---------------------------------------------------------------------------
 
+// Slots [lo, hi) are split evenly over the warps: warp w starts at
+// lo + w * per, per = ceil((hi - lo) / kWarps).  Staged vertex s, whose slots
+// are [st, en), records itself for every warp that starts inside its range (as
+// s - 1 when the warp starts on s's first slot, since that start bit counts
+// again in the expand loop).  Called for every staged vertex before the loop.
+constexpr uint32_t kNoVb = 0xFFFFFFFEu;  // real values are -1 .. kTileMax - 1
+__device__ __forceinline__ uint32_t warp_share(uint32_t lo, uint32_t hi) {
+    return (hi - lo + kWarps - 1) / kWarps;
+}
+__device__ __forceinline__ void mark_warp_starts(Smem& sm, uint32_t s, uint32_t st, uint32_t en,
+                                                 uint32_t lo, uint32_t hi) {
+    if (hi <= lo || en <= lo || st >= hi) return;
+    const uint32_t per = warp_share(lo, hi);
+    for (uint32_t w = st > lo ? (st - lo + per - 1) / per : 0u; w < (uint32_t)kWarps; ++w) {
+        const uint32_t e0 = lo + w * per;
+        if (e0 >= en || e0 >= hi) break;
+        sm.wvb[w] = e0 == st ? s - 1u : s;
+    }
+}
+
 // Expands the slots [l0, l1) of the staged vertices (cnt of them; sm.off holds
 // their first slots, sm.off[cnt] the end; sm.sbits marks the first slots that
 // fall in [l0, l1)).  Slot s of vertex t is the column entry with row index
@@ -763,13 +785,17 @@ __device__ __forceinline__ void expand_core(const Inst& I, InstCtl* ctl, const E
     // vertex(s) = vb + (number of vertex starts in [e0, s])
     uint32_t vb = 0;
     if (e0 < e1) {
-        uint32_t lo = 0, hi = cnt;  // off[lo] <= e0 < off[hi]
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (sm.off[mid] <= e0) lo = mid;
-            else hi = mid;
+        vb = sm.wvb[warp];
+        // recorded while staging; searched for only if the record is missing
+        if (vb == kNoVb || (vb != kUnset && vb >= cnt)) {
+            uint32_t lo = 0, hi = cnt;  // off[lo] <= e0 < off[hi]
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (sm.off[mid] <= e0) lo = mid;
+                else hi = mid;
+            }
+            vb = lo - (sm.off[lo] == e0 ? 1u : 0u);
         }
-        vb = lo - (sm.off[lo] == e0 ? 1u : 0u);
     }
     uint32_t starts = 0;  // vertex starts in [e0, current group base)
     // row index (kUnset: no entry in this slot) and frontier column of each group
@@ -963,6 +989,7 @@ __device__ ABFS_NOINLINE void unit_level(const Inst& I, InstCtl* ctl, const Engi
             sm.off[s] = (uint32_t)(sm.seg_eb[q] + ld_l2(I.fpre[p] + idx) - g0);
         }
         if (threadIdx.x == 0) sm.off[cnt] = (uint32_t)(sm.sub_end - g0);
+        if (threadIdx.x < (uint32_t)kWarps) sm.wvb[threadIdx.x] = kNoVb;
         // slots [lo, hi) of this sub-tile belong to the unit
         const uint32_t lo = (uint32_t)(e - g0);
         const uint32_t hi_s = (uint32_t)(min(u_hi, (unsigned long long)sm.sub_end) - g0);
@@ -974,6 +1001,7 @@ __device__ ABFS_NOINLINE void unit_level(const Inst& I, InstCtl* ctl, const Engi
             const uint32_t len = sm.off[s + 1] - st - kVertexSlots;
             sm.end[s] = st + len;
             sm.b[s] -= st;  // row index of slot x is b + x
+            mark_warp_starts(sm, s, st, st + len + kVertexSlots, lo, hi_s);
             if (st >= lo && st < hi_s) {
                 // the vertex's first slot lies in this unit: it joins the visited
                 // set of the next level's test (once), and starts a run of slots
@@ -1262,16 +1290,18 @@ __device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const
             nnz_local += (mat == 0) ? len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
         }
         for (uint32_t w = threadIdx.x; w < (uint32_t)kStartWords; w += kThreads) sm.sbits[w] = 0u;
+        if (threadIdx.x < (uint32_t)kWarps) sm.wvb[threadIdx.x] = kNoVb;
         __syncthreads();
         block_exclusive_scan<kTileItems>(sm.off, cnt, sm);
         const uint32_t S = sm.off[cnt];
         // window [l0, l1) of at most kUnitMax slots; its vertex starts in sbits
         uint32_t l0 = 0, l1 = min(S, kUnitMax);
         for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
-            const uint32_t st = sm.off[s];
-            sm.end[s] = sm.off[s + 1] - kVertexSlots;
+            const uint32_t st = sm.off[s], en = sm.off[s + 1];
+            sm.end[s] = en - kVertexSlots;
             sm.b[s] -= st;  // row index of slot x is b + x
             if (st < l1) atomicOr(&sm.sbits[st >> 5], 1u << (st & 31));
+            mark_warp_starts(sm, s, st, en, l0, l1);
         }
         __syncthreads();
         prof_add(sm, kProfNLoad, pt0);
@@ -1284,10 +1314,12 @@ __device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const
             l0 = l1;
             l1 = min(S, l0 + kUnitMax);
             for (uint32_t w = threadIdx.x; w < (uint32_t)kStartWords; w += kThreads) sm.sbits[w] = 0u;
+            if (threadIdx.x < (uint32_t)kWarps) sm.wvb[threadIdx.x] = kNoVb;
             __syncthreads();
             for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
                 const uint32_t st = sm.off[s];
                 if (st >= l0 && st < l1) atomicOr(&sm.sbits[(st - l0) >> 5], 1u << ((st - l0) & 31));
+                mark_warp_starts(sm, s, st, sm.off[s + 1], l0, l1);
             }
             __syncthreads();
         }
@@ -1383,6 +1415,9 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
     __syncthreads();
     const uint32_t sw = sm.nr_sw, mat_cur = sm.nr_mcur, mat_prev = sm.nr_mprev;
     bool lens = false;
+    // counters stay in registers until the run ends
+    Tally t;
+    uint32_t nnz_local = 0;
     // a search has at most n levels: a broken invariant ends the run instead
     // of looping
     for (uint32_t guard = I.n + 1;; --guard) {
@@ -1392,8 +1427,6 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
         const uint32_t mat_next = k + 1 >= sw ? mat_cur : mat_prev;
         // issued now, read when the level ends
         const uint32_t err = threadIdx.x == 0 ? ld_relaxed(&ctl->err) : 0u;
-        Tally t;
-        uint32_t nnz_local = 0;
         narrow_expand<MODE>(I, ctl, P, sm, k, f, lens, mat, mat_next, t, nnz_local);
         const long long pt2 = prof_now(sm);
         {
@@ -1432,10 +1465,6 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
         }
         const long long pt3 = prof_now(sm);
         prof_add(sm, kProfNAppend, pt2);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) nnz_local += __shfl_xor_sync(0xFFFFFFFFu, nnz_local, d);
-        if (lane == 0 && nnz_local) atomicAdd(&sm.st_nnz, (unsigned long long)nnz_local);
-        tally_flush(sm, t);
         if (threadIdx.x == 0) {
             const uint32_t fn = sm.nq_cnt;
             const unsigned long long slots = sm.nq_slots;
@@ -1465,6 +1494,10 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
         ++k;
     }
     const long long pt4 = prof_now(sm);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) nnz_local += __shfl_xor_sync(0xFFFFFFFFu, nnz_local, d);
+    if (lane == 0 && nnz_local) atomicAdd(&sm.st_nnz, (unsigned long long)nnz_local);
+    tally_flush(sm, t);
     narrow_to_blocks(I, ctl, P, sm, (k + 1) & 1, sm.nr_f);
     if (threadIdx.x == 0) st_relaxed(&ctl->reached, sm.nr_reached);
     stats_flush(sm, ctl);
