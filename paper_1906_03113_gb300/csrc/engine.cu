@@ -635,16 +635,15 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
                                             : ld_frozen(test_bm + (r[u] >> 5)))
                        : 0xFFFFFFFFu;
         if (VAR == kVarScan) {
-            // the (min, index) product and the claim bit as reductions: the
-            // least column still wins, and the new vertices are read off the
-            // bitmaps once the level is complete
+            // the (min, index) product as a reduction: the least column still
+            // wins, and once the level is complete the new vertices are the
+            // unvisited ones whose parent is set
 #pragma unroll
             for (int u = 0; u < L; ++u) {
                 if (!((w[u] >> (r[u] & 31)) & 1u)) {
                     ++t.unmasked;
                     ++t.claims;
                     atomicMin(I.parent + r[u], j[u]);
-                    atomicOr(write_bm + (r[u] >> 5), 1u << (r[u] & 31));
                 }
             }
             return;
@@ -1065,10 +1064,12 @@ __device__ ABFS_NOINLINE void unit_plain_mask(const Inst& I, InstCtl* ctl, const
 constexpr uint32_t kExtractWords = kThreads;
 
 // Extraction after a level k whose claims were reductions: the vertices of
-// level k+1 are the bits of the write bitmap that the test bitmap lacks
-// (V_{k+1} minus V_{k+2} in the paper's terms).  Unit u covers bitmap words
-// [u*kExtractWords, ...); each warp hands its 32 words' new vertices to the
-// frontier blocks of level k+1.  Their parents are already final.
+// level k+1 (V_{k+1} minus V_{k+2} in the paper's terms) are those outside the
+// test bitmap (not reached by level k) whose parent the level set.  Unit u
+// covers bitmap words [u*kExtractWords, ...); each warp reads the parents of
+// its 32 words' candidates (coalesced, a word at a time), hands the new
+// vertices to the frontier blocks of level k+1 and adds them to the write
+// bitmap (one store per word; the level's frontier marks are already there).
 __device__ ABFS_NOINLINE void unit_extract(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                              uint32_t k, uint32_t u) {
     const uint32_t p = k & 1, pn = p ^ 1;
@@ -1077,21 +1078,27 @@ __device__ ABFS_NOINLINE void unit_extract(const Inst& I, InstCtl* ctl, const En
     level_mats(ctl, k, mat, mat_next);
     const uint32_t w0 = u * kExtractWords + warp * 32;
     const uint32_t wi = w0 + lane;
-    uint32_t fresh = 0;
-    if (wi < I.nwords) fresh = ld_l2(I.bm[pn] + wi) & ~ld_l2(I.bm[p] + wi);
+    uint32_t cand = 0, wb = 0;
+    if (wi < I.nwords) {
+        cand = ~ld_l2(I.bm[p] + wi);
+        wb = ld_l2(I.bm[pn] + wi);
+        // no vertices past n in the last word
+        if (wi == I.nwords - 1 && (I.n & 31)) cand &= (1u << (I.n & 31)) - 1u;
+    }
+    uint32_t fresh = 0;  // lane q: the new vertices of word w0 + q
     uint32_t wc = sm.wcnt[warp];
-    uint32_t claims = 0;
     for (uint32_t q = 0; q < 32; ++q) {
-        const uint32_t bits = __shfl_sync(0xFFFFFFFFu, fresh, q);
-        if (!bits) continue;
-        const bool want = (bits >> lane) & 1u;
+        const uint32_t c = __shfl_sync(0xFFFFFFFFu, cand, q);
+        if (!c) continue;
         const uint32_t v = (w0 + q) * 32 + lane;
+        const bool want = ((c >> lane) & 1u) && ld_l2(I.parent + v) != kUnset;
+        const uint32_t bits = __ballot_sync(0xFFFFFFFFu, want);
+        if (lane == q) fresh = bits;
         if (want) I.level[v] = (int32_t)(k + 1);
         stage_warp(want, v, sm, wc);
         if (wc > (uint32_t)(kWarpBuf - 32)) warp_flush(sm, I, ctl, P, pn, mat_next, wc);
-        claims += want;
     }
-    (void)claims;
+    if (fresh) I.bm[pn][wi] = wb | fresh;
     if (lane == 0) sm.wcnt[warp] = wc;
     __syncwarp();
     cta_flush(sm, I, ctl, P, pn, mat_next);
