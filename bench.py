@@ -14,7 +14,9 @@ exchange), value = all ranks' edges / max-over-ranks time.
 --impl reference runs the CPU oracle (sorted-frontier queue BFS, one host
 core) on the same workload, bounded to a few minutes.
 --workload selects one of the other workloads (er16, grid4096, rgg22,
-batch512) for measurement runs.
+batch512, serve) for measurement runs; --workload ops prints the algebraic
+operation counts of Section 11 (Table 2's columns) measured on the device for
+the four single-graph workloads.
 """
 from __future__ import annotations
 
@@ -431,6 +433,59 @@ def bench_serve(args, ws, rank, local, torch, abfs, dist):
         print(json.dumps(line), flush=True)
 
 
+def bench_ops(args, ws, rank, torch, abfs, dist):
+    """Section 11's operation study (Table 2's columns) with the device counters.
+
+    Per graph and source: Algorithm 2's 2(n_c - 1) (Theorem 2: one nonzero per
+    reached row); the all-nonzero variant's 2 E_adj, every entry from level k into
+    level k+1 (at most 2m, Lemma 3), counted by the submatrix engine as the entries
+    that pass the mask; masked SpMSpV's 2 nnz_c, counted by the comparator as the
+    entries it multiplies; SpMV's 2 nnz L (closed form, not run).  Checks: the
+    submatrix engine reads each reached column once (Claim 1, entries read =
+    nnz_c), E_adj <= m, and the comparator multiplies exactly nnz_c entries."""
+    rows = []
+    t0 = time.perf_counter()
+    for name in ("er16", "rmat22", "grid4096", "rgg22"):
+        g, srcs, (wname, _) = make_workload(name)
+        G = abfs.graph_create(g.colptr, g.rowidx, directed=g.directed)
+        level = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
+        m = g.nnz if g.directed else g.nnz // 2
+        for s in srcs[:2]:
+            _, _, sub = abfs.run(G, int(s), level, parent, stream, abfs.default_params(), stats=True)
+            _, _, pl = abfs.run(G, int(s), level, parent, stream,
+                                abfs.default_params(mode=abfs.MODE_PLAIN), stats=True)
+            assert sub["status"] == 0 and pl["status"] == 0, (sub, pl)
+            n_c, nnz_c, L = sub["reached"], sub["nnz_reached"], sub["levels"]
+            e_adj = sub["entries_unmasked"]
+            ops = {"alg2": 2 * (n_c - 1), "alg2_all_nonzero": 2 * e_adj,
+                   "spmmspv": 2 * pl["entries_read"], "spmv": 2 * g.nnz * L}
+            checks = {"claim1_columns_once": sub["entries_read"] == nnz_c,
+                      "lemma3_e_adj_le_m": e_adj <= m,
+                      "spmmspv_eq_2nnz_c": pl["entries_read"] == nnz_c,
+                      "same_levels": pl["levels"] == L and pl["reached"] == n_c}
+            rows.append({"graph": wname, "source": int(s), "n": g.n, "m": m, "n_c": n_c,
+                         "nnz_c": nnz_c, "levels": L, "e_adj": e_adj, "ops": ops,
+                         "spmmspv_over_all_nonzero": ops["spmmspv"] / max(1, ops["alg2_all_nonzero"]),
+                         "checks": checks})
+        G.destroy()
+    ok = all(all(r["checks"].values()) for r in rows)
+    ratio = statistics.geometric_mean([r["spmmspv_over_all_nonzero"] for r in rows])
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "masked SpMSpV ops / submatrix all-nonzero ops (geometric mean)",
+            "value": ratio, "unit": "x", "n_gpus": ws, "steps": 1, "warmup": 0,
+            "ms_per_step": (time.perf_counter() - t0) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "ops_table2", "graphs": "er16, rmat22 (2 sources), grid4096, rgg22",
+                       "counts": "device counters of abfs_run with stats"},
+            "all_checks_pass": ok, "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -438,7 +493,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22",
-                    choices=["rmat22", "er16", "grid4096", "rgg22", "batch512", "serve"])
+                    choices=["rmat22", "er16", "grid4096", "rgg22", "batch512", "serve", "ops"])
     ap.add_argument("--queries", type=int, default=100000, help="serve: queries per arrival rate")
     ap.add_argument("--mode", default="sub", choices=["sub", "plain"])
     ap.add_argument("--shrink", type=float, default=0.0)
@@ -464,6 +519,8 @@ def main():
         return bench_batch(args, ws, rank, local, torch, abfs, dist)
     if args.workload == "serve":
         return bench_serve(args, ws, rank, local, torch, abfs, dist)
+    if args.workload == "ops":
+        return bench_ops(args, ws, rank, torch, abfs, dist)
 
     g, srcs, (wname, wdesc) = make_workload(args.workload)
     G = abfs.graph_create(g.colptr, g.rowidx, directed=g.directed)

@@ -20,6 +20,12 @@ Contents:
   * ``op_counts``        -- Table 2 operation counts measured by running each
                             method's loop (C).
   * ``closed_form_counts`` -- the closed forms those counts must meet.
+  * ``path_counts``      -- the all-nonzero variant of Algorithm 2 over the
+                            arithmetic semiring (Section 8, Proposition 1's
+                            caveat): x_k(v) = number of shortest paths from
+                            the source to v, mod 2^64, in numpy.
+  * ``path_counts_dense`` -- the same recurrence with dense selection matrices
+                            and exact integers, small n only.
 
 Every function is pinned by ``tests/test_oracle_pins.py`` against values the
 paper prints, closed forms, brute force and identities (Proposition 1).
@@ -289,6 +295,75 @@ def bfs_symmetric_form(g_or_M, src: int):
         x = ax & V                                      # x_{k+1} masked by V_{k+1}
         y = (Mi @ y.astype(np.int64)) > 0               # y_{k+1} = A y_k
     return steps
+
+
+def path_counts(g_or_colptr, src: int, rowidx=None) -> np.ndarray:
+    """Shortest-path counts sigma (uint64, mod 2^64) from ``src``.
+
+    Section 8 turns Algorithm 2 into its all-nonzero variant: every entry of
+    column j whose row is still unvisited contributes to the product, instead of
+    the first one only.  With the arithmetic semiring and x_1 = e_src (Proposition
+    1 asks for one semiring throughout), x_{k+1}(i) sums x_k(j) over the stored
+    entries i of the frontier columns j, for rows i of level k+1; by induction on
+    k it counts the shortest paths from the source.  A column that stores row i
+    twice counts twice (the stored matrix, read as integer entries).  Evaluated
+    level by level: the entries from level k to level k+1 are applied after
+    every entry of level k-1 to level k.  sigma[v] = 0 for unreached v."""
+    colptr, rowidx = _arrays(g_or_colptr, rowidx)
+    n = colptr.shape[0] - 1
+    nnz = int(colptr[-1])
+    level, _ = bfs(colptr, src, rowidx)
+    cols = np.repeat(np.arange(n, dtype=np.int64), np.diff(colptr.astype(np.int64)))
+    rows = rowidx[:nnz].astype(np.int64)
+    lj = level[cols].astype(np.int64)
+    keep = (lj >= 0) & (level[rows].astype(np.int64) == lj + 1)
+    cols, rows, lj = cols[keep], rows[keep], lj[keep]
+    order = np.argsort(lj, kind="stable")
+    cols, rows, lj = cols[order], rows[order], lj[order]
+    depth = int(level.max()) + 1
+    bounds = np.searchsorted(lj, np.arange(depth + 1))
+    sigma = np.zeros(n, dtype=np.uint64)
+    sigma[src] = 1
+    for k in range(depth):
+        a, b = int(bounds[k]), int(bounds[k + 1])
+        if a < b:
+            np.add.at(sigma, rows[a:b], sigma[cols[a:b]])   # wraps mod 2^64
+    return sigma
+
+
+def count_matrix(g) -> np.ndarray:
+    """A^T with integer entries: M[i, j] = copies of row i stored in column j."""
+    M = np.zeros((g.n, g.n), dtype=np.int64)
+    cols = np.repeat(np.arange(g.n), np.diff(g.colptr.astype(np.int64)))
+    np.add.at(M, (g.rowidx.astype(np.int64), cols), 1)
+    return M
+
+
+def path_counts_dense(g_or_M, src: int) -> list:
+    """Theorem 1's masked recurrence x_{k+1} = S_{k+1} M S_k x_k over the
+    arithmetic semiring (ordinary + and *, exact Python integers), x_1 = e_src,
+    M = ``count_matrix``.  Returns sigma as a list of ints: the value x_k(v) at
+    the step k where v enters a support (1 for the source, 0 if unreached).
+    Dense O(n^2) per step: small n only."""
+    M = g_or_M if isinstance(g_or_M, np.ndarray) else count_matrix(g_or_M)
+    n = M.shape[0]
+    Mo = M.astype(object)
+    V = np.ones(n, dtype=bool)                          # V_1
+    x = np.zeros(n, dtype=object)
+    x[src] = 1                                          # x_1
+    sigma = [0] * n
+    sigma[src] = 1
+    while any(v != 0 for v in x):
+        supp = np.array([v != 0 for v in x], dtype=bool)
+        V_next = V & ~supp                              # V_{k+1} = V_k \ supp(x_k)
+        xs = np.where(V, x, 0)                          # S_k x_k
+        y = Mo.dot(xs)                                  # M S_k x_k
+        x = np.where(V_next, y, 0)                      # S_{k+1} M S_k x_k
+        for v in range(n):
+            if x[v] != 0:
+                sigma[v] = int(x[v])
+        V = V_next
+    return sigma
 
 
 def floyd_warshall(M: np.ndarray) -> np.ndarray:
