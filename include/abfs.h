@@ -59,7 +59,7 @@ typedef enum {
     ABFS_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out; the kernel returned */
     ABFS_ERR_BUSY = 6,          /* serving: the request was not admitted (no slot / memory) */
     ABFS_ERR_DEVICE = 7,        /* a device-side consistency check failed (capacity, bounds) */
-    ABFS_ERR_UNSUPPORTED = 8,   /* size beyond this build's limits */
+    ABFS_ERR_UNSUPPORTED = 8,   /* size beyond this build's limits, or a feature the mode lacks */
     ABFS_ERR_NOT_FOUND = 9      /* serving: unknown ticket */
 } abfs_status;
 
@@ -160,6 +160,23 @@ int abfs_graph_footprint(abfs_graph_t g, const abfs_params* params, size_t* byte
  */
 int abfs_run(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,
              abfs_stream_t stream, const abfs_params* params, abfs_stats* stats);
+
+/*
+ * One search that also counts shortest paths: the all-nonzero variant of
+ * Algorithm 2 (Section 8) over the arithmetic semiring, which Proposition 1
+ * requires to be used at every step.  With x_1 = e_source, every entry (i, j)
+ * of A[V_{k+1}, V_k] (j on level k, row i not yet visited) adds x_k(j) into
+ * x_{k+1}(i), so x_{k+1}(i) = sigma[i] is the number of shortest paths from
+ * the source to i.  sigma is a caller-owned DEVICE buffer of n uint64, written
+ * modulo 2^64; sigma[source] = 1, unreached vertices 0.  A column that stores
+ * row i twice counts as the integer entry 2.  level/parent as in abfs_run
+ * (same values).  Submatrix mode only (ABFS_ERR_UNSUPPORTED for the
+ * comparator); a NULL sigma is ABFS_ERR_INVALID_ARG.  Cost over abfs_run: one
+ * 64-bit load and one 64-bit atomic add per multiplied entry (E_adj of them).
+ */
+int abfs_run_counts(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,
+                    uint64_t* sigma, abfs_stream_t stream, const abfs_params* params,
+                    abfs_stats* stats);
 
 /*
  * Same search, end to end through host memory: copies the source in, runs,

@@ -22,6 +22,7 @@ from .binding import (  # noqa: F401
     graph_destroy,
     load,
     run,
+    run_counts,
     run_batch,
     run_host,
     run_trace,

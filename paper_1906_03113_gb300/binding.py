@@ -142,6 +142,7 @@ def load():
         "abfs_graph_info": ([vp, P(u32), P(u64), P(c_int)], c_int),
         "abfs_graph_footprint": ([vp, P(Params), P(ctypes.c_size_t)], c_int),
         "abfs_run": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
+        "abfs_run_counts": ([vp, u32, vp, vp, vp, vp, P(Params), P(Stats)], c_int),
         "abfs_run_host": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
         "abfs_run_trace": ([vp, u32, vp, vp, vp, P(Params), vp, u32, P(u32)], c_int),
         "abfs_run_batch": ([P(vp), P(u32), u32, P(vp), P(vp), vp, P(Params), P(i32)], c_int),
@@ -284,6 +285,26 @@ def run(g: Graph, source: int, level=None, parent=None, stream=None, params: Par
                          ctypes.byref(st) if st else None)
     _check(rc, "abfs_run")
     return (level, parent, st.as_dict()) if stats else (level, parent)
+
+
+def run_counts(g: Graph, source: int, level=None, parent=None, sigma=None, stream=None,
+               params: Params | None = None, stats: bool = False):
+    """abfs_run_counts: (level, parent, sigma) CUDA tensors -- int32, int32 and
+    int64 holding the uint64 shortest-path counts mod 2^64 -- (and a stats dict)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    level, parent = _outputs(g.n, level, parent, dev)
+    if sigma is None:
+        sigma = torch.empty(g.n, dtype=torch.int64, device=dev)
+    if sigma.numel() < g.n or sigma.element_size() != 8 or not sigma.is_cuda:
+        raise ValueError("sigma must be a CUDA tensor of n 64-bit integers")
+    st = Stats() if stats else None
+    rc = load().abfs_run_counts(g.handle, int(source), level.data_ptr(), parent.data_ptr(),
+                                sigma.data_ptr(), _stream_ptr(stream),
+                                ctypes.byref(params) if params else None,
+                                ctypes.byref(st) if st else None)
+    _check(rc, "abfs_run_counts")
+    return (level, parent, sigma, st.as_dict()) if stats else (level, parent, sigma)
 
 
 TRACE_KINDS = {0: "level", 1: "plain_mult", 2: "plain_mask", 3: "shrink", 4: "init",

@@ -389,13 +389,14 @@ const abfs_params& pick_params(const abfs_graph_s* g, const abfs_params* params,
 // Enqueues one search into g's workspace; caller holds g->mu.
 int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* parent,
                    cudaStream_t s, const abfs_params& p, uint4* trace = nullptr,
-                   uint32_t trace_cap = 0, unsigned long long* prof = nullptr) {
+                   uint32_t trace_cap = 0, unsigned long long* prof = nullptr,
+                   uint64_t* sigma = nullptr) {
     int rc = ensure_workspace(g, p);
     if (rc) return rc;
     Workspace& w = g->ws;
     if (g->used) CK(cudaStreamWaitEvent(s, g->last_use, 0));
-    CK(launch_set_query(w.d_inst, source, level, reinterpret_cast<uint32_t*>(parent), trace,
-                        trace_cap, s));
+    CK(launch_set_query(w.d_inst, source, level, reinterpret_cast<uint32_t*>(parent),
+                        reinterpret_cast<unsigned long long*>(sigma), trace, trace_cap, s));
     EngineArgs a;
     a.insts = w.d_inst;
     a.ninst = 1;
@@ -541,6 +542,23 @@ extern "C" int abfs_run(abfs_graph_t g, uint32_t source, int32_t* level, int32_t
     return ABFS_OK;
 }
 
+extern "C" int abfs_run_counts(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,
+                               uint64_t* sigma, abfs_stream_t stream, const abfs_params* params,
+                               abfs_stats* stats) {
+    if (!g || !level || !parent || !sigma || source >= g->n) return ABFS_ERR_INVALID_ARG;
+    abfs_params tmp;
+    const abfs_params& p = pick_params(g, params, tmp);
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p.mode != ABFS_MODE_SUBMATRIX) return ABFS_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    rc = enqueue_single(g, source, level, parent, s, p, nullptr, 0, nullptr, sigma);
+    if (rc) return rc;
+    if (stats) return finish_stats(g, s, stats);
+    return ABFS_OK;
+}
+
 extern "C" int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_host,
                              int32_t* parent_host, abfs_stream_t stream, const abfs_params* params,
                              abfs_stats* stats) {
@@ -615,7 +633,7 @@ extern "C" int abfs_run_trace(abfs_graph_t g, uint32_t source, int32_t* level, i
         }
         *count = (cap > kProfEntries) ? n + kProfEntries : n;
         // the workspace descriptor keeps no pointer to the freed trace buffer
-        launch_set_query(g->ws.d_inst, 0, nullptr, nullptr, nullptr, 0, s);
+        launch_set_query(g->ws.d_inst, 0, nullptr, nullptr, nullptr, nullptr, 0, s);
         cudaStreamSynchronize(s);
     }
     dev_free(d_trace);

@@ -627,6 +627,10 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
     if (MODE == kModeSub) {
         const uint32_t* test_bm = I.bm[p];
         uint32_t* write_bm = I.bm[p ^ 1];
+        // all-nonzero variant over the arithmetic semiring (shortest-path
+        // counts): every entry that passes the mask adds x_k(j) = sigma[j],
+        // final since level k-1 completed, into sigma[r]
+        unsigned long long* const sigma = I.sigma;
         uint32_t w[L];
 #pragma unroll
         for (int u = 0; u < L; ++u)
@@ -644,6 +648,7 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
                     ++t.unmasked;
                     ++t.claims;
                     atomicMin(I.parent + r[u], j[u]);
+                    if (sigma) atomicAdd(sigma + r[u], ld_l2(sigma + j[u]));
                 }
             }
             return;
@@ -659,6 +664,7 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
                 ++t.unmasked;
                 ++t.claims;
                 win[u] = atomicMin(I.parent + r[u], j[u]) == kUnset;
+                if (sigma) atomicAdd(sigma + r[u], ld_l2(sigma + j[u]));
             }
         }
 #pragma unroll
@@ -1194,6 +1200,7 @@ __device__ ABFS_NOINLINE void unit_init(const Inst& I, const EngineParams& P, ui
         I.level[v] = -1;
         I.parent[v] = kUnset;
         if (P.mode == kModePlain) I.y[v] = ~0ull;
+        if (I.sigma) I.sigma[v] = 0ull;
     }
     if (P.mode == kModeSub) {
         const uint32_t w0 = v0 >> 5, w1 = (v1 + 31) >> 5;  // init_tile is a multiple of 32
@@ -1524,6 +1531,7 @@ __device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const Eng
         const uint32_t s = I.src;
         I.level[s] = 0;
         I.parent[s] = s;
+        if (I.sigma) I.sigma[s] = 1ull;
         if (MODE == kModeSub) atomicOr(I.bm[0] + (s >> 5), 1u << (s & 31));
         const uint32_t b0 = ld_ro(I.colptr + s);
         const uint32_t w = ld_ro(I.colptr + s + 1) - b0 + kVertexSlots;
@@ -1941,6 +1949,7 @@ __global__ void init_fill_kernel(const Inst* insts, uint32_t ninst, uint32_t mod
         I.level[v] = -1;
         I.parent[v] = kUnset;
         if (mode == kModePlain) I.y[v] = ~0ull;
+        if (I.sigma) I.sigma[v] = 0ull;
     }
     if (mode == kModeSub) {
         for (uint32_t w = t0; w < I.nwords; w += stride) {
@@ -1967,6 +1976,7 @@ __global__ void init_source_kernel(EngineArgs a) {
     const uint32_t s = I.src;
     I.level[s] = 0;
     I.parent[s] = s;
+    if (I.sigma) I.sigma[s] = 1ull;  // x_1 = e_src over the arithmetic semiring
     if (P.mode == kModeSub) I.bm[0][s >> 5] |= 1u << (s & 31);  // V_2 = V_1 \ {source}
     // frontier of level 0: one block holding the source
     const uint32_t len = I.colptr[s + 1] - I.colptr[s];
@@ -2005,17 +2015,19 @@ __global__ void init_source_kernel(EngineArgs a) {
 // Writes the per-call fields of instance 0 (single searches reuse one
 // descriptor; kernel arguments avoid a host staging buffer).
 __global__ void set_query_kernel(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
-                                 uint4* trace, uint32_t trace_cap) {
+                                 unsigned long long* sigma, uint4* trace, uint32_t trace_cap) {
     inst->src = src;
     inst->level = level;
     inst->parent = parent;
+    inst->sigma = sigma;
     inst->trace = trace;
     inst->trace_cap = trace_cap;
 }
 
 cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
-                             uint4* trace, uint32_t trace_cap, cudaStream_t s) {
-    set_query_kernel<<<1, 1, 0, s>>>(inst, src, level, parent, trace, trace_cap);
+                             unsigned long long* sigma, uint4* trace, uint32_t trace_cap,
+                             cudaStream_t s) {
+    set_query_kernel<<<1, 1, 0, s>>>(inst, src, level, parent, sigma, trace, trace_cap);
     return cudaGetLastError();
 }
 

@@ -128,6 +128,7 @@ struct Inst {
     unsigned long long ucap; // unit starts per frontier
     int32_t* level;          // output
     uint32_t* parent;        // output (0xFFFFFFFF reads as -1)
+    unsigned long long* sigma;  // optional output: shortest-path counts mod 2^64 (nullptr = off)
     uint32_t* bm[2];         // visited bitmaps, ping-pong by level parity
     uint32_t* fq[2];         // frontier vertices, by level parity
     uint32_t* fbeg[2];       // their column begins (kUnset: no entries)
@@ -227,6 +228,7 @@ int graph_arrays(abfs_graph_t g, const uint32_t** colptr, const uint32_t** rowid
 // Launch helpers implemented in engine.cu.
 cudaError_t launch_put_inst(const Inst& inst, Inst* dst, cudaStream_t s);
 cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
+                             unsigned long long* sigma,
                              uint4* trace, uint32_t trace_cap, cudaStream_t s);
 cudaError_t launch_init(const EngineArgs& a, uint32_t max_n, cudaStream_t s);
 cudaError_t launch_engine(const EngineArgs& a, int grid, cudaStream_t s);
