@@ -93,6 +93,18 @@ typedef struct {
                                  slots multiplies and claims by reductions (no returned
                                  values), and a scan of the visited bitmaps then collects the
                                  vertices it reached; 0: never */
+    uint32_t bottom_up_alpha; /* hybrid (direction optimisation, not the paper's method): 0 =
+                                 off.  Otherwise a level runs bottom-up -- each unvisited
+                                 vertex scans its column for the least frontier index and
+                                 stops at the first hit -- once the frontier's edges m_f
+                                 satisfy m_f * alpha > m_u (edges of vertices not reached
+                                 yet), until the frontier's size n_f satisfies
+                                 n_f * beta < n.  Results are identical.  Applies to
+                                 undirected graphs whose columns ascend (checked at
+                                 abfs_graph_create) in abfs_run / abfs_run_host; other
+                                 searches stay top-down.  Submatrix mode without physical
+                                 shrink only (else ABFS_ERR_INVALID_ARG). */
+    uint32_t bottom_up_beta;  /* see bottom_up_alpha */
 } abfs_params;
 
 /* Per-search counters, filled when a stats pointer is passed. */
@@ -192,6 +204,7 @@ int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_host, int32_t*
  *   [0..1] %globaltimer (ns, low/high), [2] phase kind << 24 | BFS level
  *   (kind 0 level, 1 comparator multiply, 2 comparator mask, 3 shrink,
  *   5 level claimed by reductions, 6 extraction of its new vertices,
+ *   7 frontier bitmap of a bottom-up level, 8 bottom-up level,
  *   0xFE start, 0xFF end), [3] 0 if the phase was published to the whole
  *   grid, 1 if it ran on one CTA, 2 if it is a further level of a resident
  *   narrow run, [4] units or touched rows of the phase, [5] frontier

@@ -47,6 +47,8 @@ class Params(ctypes.Structure):
         ("timeout_ms", ctypes.c_uint32),
         ("narrow_resident", ctypes.c_uint32),
         ("claim_scan", ctypes.c_uint32),
+        ("bottom_up_alpha", ctypes.c_uint32),
+        ("bottom_up_beta", ctypes.c_uint32),
     ]
 
     def as_dict(self) -> dict:
@@ -308,7 +310,8 @@ def run_counts(g: Graph, source: int, level=None, parent=None, sigma=None, strea
 
 
 TRACE_KINDS = {0: "level", 1: "plain_mult", 2: "plain_mask", 3: "shrink", 4: "init",
-               5: "level_scan", 6: "extract", 0xFE: "start", 0xFF: "end"}
+               5: "level_scan", 6: "extract", 7: "bu_prep", 8: "bottom_up", 0xFE: "start",
+               0xFF: "end"}
 
 
 def run_trace(g: Graph, source: int, params: Params | None = None, cap: int = 4096, stream=None):

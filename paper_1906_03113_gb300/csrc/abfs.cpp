@@ -125,6 +125,8 @@ abfs_params default_params() {
     p.timeout_ms = 10000;
     p.narrow_resident = 1;
     p.claim_scan = 1u << 22;
+    p.bottom_up_alpha = 0;
+    p.bottom_up_beta = 24;
     return p;
 }
 
@@ -142,6 +144,9 @@ int check_params(const abfs_params& p) {
     if (!(p.shrink_theta >= 0.f) || p.shrink_theta > 1.f) return ABFS_ERR_INVALID_ARG;
     if (p.timeout_ms < 1 || p.timeout_ms > 600000) return ABFS_ERR_INVALID_ARG;
     if (p.narrow_resident > 1) return ABFS_ERR_INVALID_ARG;
+    // the hybrid reads the input columns: submatrix mode, no physical shrink
+    if (p.bottom_up_alpha && (p.mode != ABFS_MODE_SUBMATRIX || shrink_enabled(p)))
+        return ABFS_ERR_INVALID_ARG;
     return ABFS_OK;
 }
 
@@ -156,6 +161,8 @@ EngineParams engine_params(const abfs_params& p) {
     e.narrow_edges = p.narrow_edges;
     e.narrow_loop = p.narrow_resident;
     e.scan_min = p.mode == ABFS_MODE_SUBMATRIX ? p.claim_scan : 0u;
+    e.bu_alpha = p.mode == ABFS_MODE_SUBMATRIX ? p.bottom_up_alpha : 0u;
+    e.bu_beta = p.bottom_up_beta;
     e.shrink_theta = shrink_enabled(p) ? p.shrink_theta : 0.f;
     e.shrink_max = shrink_enabled(p) ? std::min<uint32_t>(p.shrink_max, 64) : 0;
     e.shrink_tile = kTileMax;
@@ -197,6 +204,8 @@ Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p) {
     }
     if (p.mode == ABFS_MODE_SUBMATRIX)
         for (int i = 0; i < 2; ++i) L.bm[i] = take((size_t)L.nwords * 4);
+    if (p.mode == ABFS_MODE_SUBMATRIX)
+        for (int i = 0; i < 2; ++i) L.fbm[i] = take((size_t)L.nwords * 4);
     if (p.mode == ABFS_MODE_PLAIN) {
         L.y = take((size_t)n * 8);
         L.touched = take((size_t)n * 4);
@@ -234,6 +243,7 @@ Inst make_inst_raw(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, c
         I.blk[i] = reinterpret_cast<Block*>(base + L.blk[i]);
         I.ustart[i] = reinterpret_cast<uint2*>(base + L.ustart[i]);
         I.bm[i] = L.bm[i] ? reinterpret_cast<uint32_t*>(base + L.bm[i]) : nullptr;
+        I.fbm[i] = L.fbm[i] ? reinterpret_cast<uint32_t*>(base + L.fbm[i]) : nullptr;
     }
     if (L.y) I.y = reinterpret_cast<unsigned long long*>(base + L.y);
     if (L.touched) I.touched = reinterpret_cast<uint32_t*>(base + L.touched);
@@ -276,6 +286,7 @@ struct abfs_graph_s {
     uint32_t n = 0;
     uint64_t nnz = 0;
     int directed = 0;
+    bool sorted = false;          // every column's row indices ascend (bottom-up levels allowed)
     int device = 0;
     int sms = 0;
     bool tuned = false;
@@ -395,8 +406,9 @@ int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* pa
     if (rc) return rc;
     Workspace& w = g->ws;
     if (g->used) CK(cudaStreamWaitEvent(s, g->last_use, 0));
+    const uint32_t bu_ok = (!g->directed && g->sorted && !sigma) ? 1u : 0u;
     CK(launch_set_query(w.d_inst, source, level, reinterpret_cast<uint32_t*>(parent),
-                        reinterpret_cast<unsigned long long*>(sigma), trace, trace_cap, s));
+                        reinterpret_cast<unsigned long long*>(sigma), bu_ok, trace, trace_cap, s));
     EngineArgs a;
     a.insts = w.d_inst;
     a.ninst = 1;
@@ -486,7 +498,16 @@ extern "C" int abfs_graph_create(const uint32_t* colptr, const uint32_t* rowidx,
     const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaError_t e = cudaMemcpyAsync(g->d_colptr, colptr, ((size_t)n + 1) * 4, kind, s);
     if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(g->d_rowidx, rowidx, nnz * 4, kind, s);
+    // whether every column ascends (the hybrid's bottom-up levels need it)
+    uint32_t* d_flag = nullptr;
+    if (e == cudaSuccess && dev_alloc((void**)&d_flag, 4) != ABFS_OK) e = cudaErrorMemoryAllocation;
+    uint32_t unsorted = 1;
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, 4, s);
+    if (e == cudaSuccess) e = launch_sorted_check(g->d_colptr, g->d_rowidx, n, d_flag, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&unsorted, d_flag, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(d_flag);
+    g->sorted = unsorted == 0;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->last_use, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         abfs_graph_destroy(g);
@@ -633,7 +654,7 @@ extern "C" int abfs_run_trace(abfs_graph_t g, uint32_t source, int32_t* level, i
         }
         *count = (cap > kProfEntries) ? n + kProfEntries : n;
         // the workspace descriptor keeps no pointer to the freed trace buffer
-        launch_set_query(g->ws.d_inst, 0, nullptr, nullptr, nullptr, nullptr, 0, s);
+        launch_set_query(g->ws.d_inst, 0, nullptr, nullptr, nullptr, 0u, nullptr, 0, s);
         cudaStreamSynchronize(s);
     }
     dev_free(d_trace);

@@ -1105,8 +1105,126 @@ __device__ ABFS_NOINLINE void unit_extract(const Inst& I, InstCtl* ctl, const En
         if (wc > (uint32_t)(kWarpBuf - 32)) warp_flush(sm, I, ctl, P, pn, mat_next, wc);
     }
     if (fresh) I.bm[pn][wi] = wb | fresh;
+    // hybrid: the frontier bitmap of level k+1, in case it runs bottom-up
+    if (P.bu_alpha && I.bu_ok && wi < I.nwords) I.fbm[pn][wi] = fresh;
     if (lane == 0) sm.wcnt[warp] = wc;
     __syncwarp();
+    cta_flush(sm, I, ctl, P, pn, mat_next);
+}
+
+// ---------------------------------------------------------------------------
+// hybrid: bottom-up levels (direction optimisation; not the paper's method)
+// ---------------------------------------------------------------------------
+//
+// For an undirected graph whose columns are sorted, the product of a level can
+// also be evaluated row by row: x_{k+1}(i) for an unvisited row i is the least
+// frontier index j in column i (= row i, A symmetric), and with the column
+// ascending the first frontier entry is that least index, so the scan stops
+// there.  The result (levels and min-index parents) is the submatrix method's;
+// only the order of evaluation changes.  The frontier of level k is read from
+// a bitmap (fbm[k & 1]).
+
+constexpr uint32_t kBuWarpWords = 8;                  // bitmap words per warp in a unit
+constexpr uint32_t kBuWords = kWarps * kBuWarpWords;  // bitmap words per unit
+constexpr uint32_t kBuLaneBatches = 4;                // lane-serial scan: 4 batches of 4 entries
+
+// Frontier bitmap of level k after a top-down level: at the start of level k
+// the test bitmap holds the levels <= k and the write bitmap the levels < k.
+__device__ ABFS_NOINLINE void unit_bu_prep(const Inst& I, uint32_t k, uint32_t u) {
+    const uint32_t p = k & 1;
+    const uint32_t w1 = min(I.nwords, (u + 1) * kExtractWords);
+    for (uint32_t w = u * kExtractWords + threadIdx.x; w < w1; w += kThreads)
+        I.fbm[p][w] = ld_l2(I.bm[p] + w) & ~ld_l2(I.bm[p ^ 1] + w);
+}
+
+// Bottom-up level k over bitmap words [u*kBuWords, ...): each lane takes one
+// unvisited vertex of a word and scans the first entries of its column itself,
+// four at a time; columns still unresolved after that are scanned by the whole
+// warp, 32 entries at a time.  Found vertices get level k+1 and their parent,
+// go to the frontier blocks of level k+1, the write bitmap (one store per word:
+// test | new = the levels <= k+1) and the next frontier bitmap.
+__device__ ABFS_NOINLINE void unit_bottom_up(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                             Smem& sm, uint32_t k, uint32_t u) {
+    const uint32_t p = k & 1, pn = p ^ 1;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t mat, mat_next;
+    level_mats(ctl, k, mat, mat_next);
+    const uint32_t* fbm = I.fbm[p];
+    const uint32_t w0 = u * kBuWords + warp * kBuWarpWords;
+    const uint32_t wi = w0 + lane;
+    const bool own = lane < kBuWarpWords && wi < I.nwords;
+    uint32_t tb = 0, cand = 0;
+    if (own) {
+        tb = ld_frozen(I.bm[p] + wi);
+        cand = ~tb;
+        if (wi == I.nwords - 1 && (I.n & 31)) cand &= (1u << (I.n & 31)) - 1u;
+    }
+    Tally t;
+    uint32_t fresh = 0;  // lane q: the new vertices of word w0 + q
+    uint32_t wc = sm.wcnt[warp];
+    for (uint32_t q = 0; q < kBuWarpWords; ++q) {
+        const uint32_t c = __shfl_sync(0xFFFFFFFFu, cand, q);
+        if (!c) continue;
+        const uint32_t v = (w0 + q) * 32 + lane;
+        uint32_t e = 0, end = 0, par = kUnset;
+        if ((c >> lane) & 1u) {
+            e = ld_ro(I.colptr + v);
+            end = ld_ro(I.colptr + v + 1);
+        }
+        for (uint32_t b = 0; b < kBuLaneBatches && e < end; ++b) {
+            uint32_t jj[4], fw[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) jj[x] = e + x < end ? ld_ro(I.rowidx + e + x) : kUnset;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) fw[x] = jj[x] != kUnset ? ld_frozen(fbm + (jj[x] >> 5)) : 0u;
+            t.read += min(4u, end - e);
+#pragma unroll
+            for (int x = 3; x >= 0; --x)
+                if ((fw[x] >> (jj[x] & 31)) & 1u) par = jj[x];
+            e = par != kUnset ? end : e + 4;
+        }
+        bool defer = par == kUnset && e < end;
+        uint32_t dm;
+        while ((dm = __ballot_sync(0xFFFFFFFFu, defer)) != 0u) {
+            const uint32_t ldr = __ffs(dm) - 1;
+            const uint32_t le = __shfl_sync(0xFFFFFFFFu, e, ldr);
+            const uint32_t lend = __shfl_sync(0xFFFFFFFFu, end, ldr);
+            uint32_t found = kUnset;
+            for (uint32_t x = le; x < lend; x += 32) {
+                const uint32_t idx = x + lane;
+                const uint32_t j = idx < lend ? ld_ro(I.rowidx + idx) : kUnset;
+                const bool hit = j != kUnset && ((ld_frozen(fbm + (j >> 5)) >> (j & 31)) & 1u);
+                const uint32_t hb = __ballot_sync(0xFFFFFFFFu, hit);
+                if (lane == 0) t.read += min(32u, lend - x);
+                if (hb) {
+                    found = __shfl_sync(0xFFFFFFFFu, j, __ffs(hb) - 1);
+                    break;
+                }
+            }
+            if (lane == ldr) {
+                par = found;
+                defer = false;
+            }
+        }
+        const bool got = par != kUnset;
+        if (got) {
+            I.parent[v] = par;
+            I.level[v] = (int32_t)(k + 1);
+            ++t.unmasked;
+            ++t.claims;
+        }
+        const uint32_t bits = __ballot_sync(0xFFFFFFFFu, got);
+        if (lane == q) fresh = bits;
+        stage_warp(got, v, sm, wc);
+        if (wc > (uint32_t)(kWarpBuf - 32)) warp_flush(sm, I, ctl, P, pn, mat_next, wc);
+    }
+    if (own) {
+        I.bm[pn][wi] = tb | fresh;
+        I.fbm[pn][wi] = fresh;
+    }
+    if (lane == 0) sm.wcnt[warp] = wc;
+    __syncwarp();
+    tally_flush(sm, t);
     cta_flush(sm, I, ctl, P, pn, mat_next);
 }
 
@@ -1229,6 +1347,10 @@ __device__ void run_unit(const Inst& I, InstCtl* ctl, const EngineParams& P, Sme
         unit_plain_mask(I, ctl, P, sm, k, unit, nitems);
     } else if (kind == kPhExtract) {
         unit_extract(I, ctl, P, sm, k, unit);
+    } else if (kind == kPhBuPrep) {
+        unit_bu_prep(I, k, unit);
+    } else if (MODE == kModeSub && kind == kPhBottomUp) {
+        unit_bottom_up(I, ctl, P, sm, k, unit);
     } else if (MODE == kModeSub && kind == kPhLevelScan) {
         unit_level<MODE, kVarScan>(I, ctl, P, sm, k, unit, nitems);
     } else {
@@ -1551,6 +1673,9 @@ __device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const Eng
         // the new vertices of a level claimed by reductions are read off the bitmaps
         nkind = kPhExtract;
         nk = k;
+    } else if (kind == kPhBuPrep) {
+        nkind = kPhBottomUp;
+        nk = k;
     } else if (kind == kPhPlainMult) {
         // comparator: the mask phase of the same level follows the multiply
         const uint32_t t = ld_relaxed(&ctl->tcnt);
@@ -1601,6 +1726,25 @@ __device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const Eng
             } else {
                 nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
                 nk = k + 1;
+                if (MODE == kModeSub && P.bu_alpha && I.bu_ok && kind != kPhShrink) {
+                    // hybrid direction choice from the frontier's edges m_f and the
+                    // edges of vertices not reached yet m_u: bottom-up once
+                    // m_f * alpha > m_u, back to top-down once n_f * beta < n
+                    const unsigned long long ne1 = ld_relaxed64(&ctl->bctr[pn]) >> kBlockBits;
+                    const unsigned long long mf = ne1 - (unsigned long long)kVertexSlots * nf;
+                    const unsigned long long seen = ld_relaxed64(&ctl->nnz_reached) + mf;
+                    const unsigned long long nnz = ld_ro(I.colptr + I.n);
+                    const unsigned long long mu = nnz > seen ? nnz - seen : 0ull;
+                    uint32_t bu = ld_relaxed(&ctl->bu_on);
+                    bu = bu ? ((unsigned long long)nf * P.bu_beta >= I.n)
+                            : (mf * (unsigned long long)P.bu_alpha > mu);
+                    st_relaxed(&ctl->bu_on, bu);
+                    if (bu) {
+                        // the frontier's columns are never expanded: count them here
+                        atomicAdd(&ctl->nnz_reached, mf);
+                        nkind = (kind == kPhExtract || kind == kPhBottomUp) ? kPhBottomUp : kPhBuPrep;
+                    }
+                }
             }
         }
     }
@@ -1656,8 +1800,11 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
         } else if (nkind == kPhPlainMask) {
             units = (ni + P.tile - 1) / P.tile;
             alone = ni <= P.narrow_max;
-        } else if (nkind == kPhExtract) {
+        } else if (nkind == kPhExtract || nkind == kPhBuPrep) {
             units = (I.nwords + kExtractWords - 1) / kExtractWords;
+            alone = units <= 1;
+        } else if (nkind == kPhBottomUp) {
+            units = (I.nwords + kBuWords - 1) / kBuWords;
             alone = units <= 1;
         } else {
             // a level (or the comparator's multiply) over the frontier of level nk;
@@ -2015,19 +2162,47 @@ __global__ void init_source_kernel(EngineArgs a) {
 // Writes the per-call fields of instance 0 (single searches reuse one
 // descriptor; kernel arguments avoid a host staging buffer).
 __global__ void set_query_kernel(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
-                                 unsigned long long* sigma, uint4* trace, uint32_t trace_cap) {
+                                 unsigned long long* sigma, uint32_t bu_ok, uint4* trace,
+                                 uint32_t trace_cap) {
     inst->src = src;
     inst->level = level;
     inst->parent = parent;
     inst->sigma = sigma;
+    inst->bu_ok = bu_ok;
     inst->trace = trace;
     inst->trace_cap = trace_cap;
 }
 
 cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
-                             unsigned long long* sigma, uint4* trace, uint32_t trace_cap,
-                             cudaStream_t s) {
-    set_query_kernel<<<1, 1, 0, s>>>(inst, src, level, parent, sigma, trace, trace_cap);
+                             unsigned long long* sigma, uint32_t bu_ok, uint4* trace,
+                             uint32_t trace_cap, cudaStream_t s) {
+    set_query_kernel<<<1, 1, 0, s>>>(inst, src, level, parent, sigma, bu_ok, trace, trace_cap);
+    return cudaGetLastError();
+}
+
+// Sets *unsorted to 1 if some column's row indices descend (one warp per
+// column, 32 neighbouring pairs at a time).
+__global__ void sorted_check_kernel(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n,
+                                    uint32_t* unsorted) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (blockDim.x / 32);
+    for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) / 32; v < n; v += warps) {
+        const uint32_t b = colptr[v], e = colptr[v + 1];
+        bool bad = false;
+        for (uint32_t x = b + 1 + lane; x < e; x += 32) bad |= rowidx[x] < rowidx[x - 1];
+        if (__any_sync(0xFFFFFFFFu, bad)) {
+            if (lane == 0) *unsorted = 1u;
+            return;
+        }
+    }
+}
+
+cudaError_t launch_sorted_check(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n,
+                                uint32_t* unsorted, cudaStream_t s) {
+    uint32_t blocks = (n + 7) / 8;
+    if (blocks > 2048) blocks = 2048;
+    if (blocks == 0) blocks = 1;
+    sorted_check_kernel<<<blocks, 256, 0, s>>>(colptr, rowidx, n, unsorted);
     return cudaGetLastError();
 }
 

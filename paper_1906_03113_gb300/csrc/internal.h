@@ -69,6 +69,8 @@ enum PhaseKind : uint32_t {
     kPhInit = 4,       // serving: clear the outputs and bitmaps of a newly started search
     kPhLevelScan = 5,  // submatrix method, large level: mask, multiply and claim by reductions
     kPhExtract = 6,    // the vertices a kPhLevelScan level reached, read off the bitmaps
+    kPhBuPrep = 7,     // hybrid: the frontier bitmap of a bottom-up level that follows a top-down one
+    kPhBottomUp = 8,   // hybrid: unvisited vertices scan their sorted columns for a frontier entry
 };
 
 enum InstStatus : uint32_t { kIdle = 0, kRunning = 1, kDone = 2, kFailed = 3 };
@@ -108,7 +110,7 @@ struct InstCtl {
     uint32_t mat_switch;         // first level that reads mat_cur
     uint32_t shrink_out;         // shrink: entries written so far
     uint32_t trace_n;            // trace entries written
-    uint32_t pad_;
+    uint32_t bu_on;              // hybrid: 1 while levels run bottom-up
     unsigned long long entries_read;
     unsigned long long entries_unmasked;
     unsigned long long claims;
@@ -130,6 +132,8 @@ struct Inst {
     uint32_t* parent;        // output (0xFFFFFFFF reads as -1)
     unsigned long long* sigma;  // optional output: shortest-path counts mod 2^64 (nullptr = off)
     uint32_t* bm[2];         // visited bitmaps, ping-pong by level parity
+    uint32_t* fbm[2];        // hybrid: frontier bitmaps of bottom-up levels, by level parity
+    uint32_t bu_ok;          // hybrid: bottom-up levels allowed (undirected, sorted columns, no counts)
     uint32_t* fq[2];         // frontier vertices, by level parity
     uint32_t* fbeg[2];       // their column begins (kUnset: no entries)
     uint32_t* fpre[2];       // their entry offsets within their block
@@ -158,6 +162,8 @@ struct EngineParams {
     uint32_t narrow_edges;
     uint32_t narrow_loop;          // 1: narrow levels run back to back on one CTA (resident runs)
     uint32_t scan_min;             // wide levels with >= scan_min entry slots claim by reductions (0: never)
+    uint32_t bu_alpha;             // hybrid: top-down -> bottom-up when frontier edges * alpha > unexplored edges (0: off)
+    uint32_t bu_beta;              // hybrid: bottom-up -> top-down when frontier vertices * beta < n
     float shrink_theta;
     uint32_t shrink_max;
     uint32_t shrink_tile;          // vertices per shrink unit
@@ -206,7 +212,7 @@ enum ProfSlot : int {
 
 // Per-search workspace layout: byte offsets of each buffer from the base.
 struct Layout {
-    size_t bm[2], fq[2], fbeg[2], fpre[2], blk[2], ustart[2], y, touched, sbeg[2], slen[2],
+    size_t bm[2], fbm[2], fq[2], fbeg[2], fpre[2], blk[2], ustart[2], y, touched, sbeg[2], slen[2],
         srows[2], ctl, inst;
     size_t total;
     uint32_t nwords, bcap, ncopies;
@@ -227,8 +233,10 @@ int graph_arrays(abfs_graph_t g, const uint32_t** colptr, const uint32_t** rowid
 
 // Launch helpers implemented in engine.cu.
 cudaError_t launch_put_inst(const Inst& inst, Inst* dst, cudaStream_t s);
+cudaError_t launch_sorted_check(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n,
+                                uint32_t* unsorted, cudaStream_t s);
 cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
-                             unsigned long long* sigma,
+                             unsigned long long* sigma, uint32_t bu_ok,
                              uint4* trace, uint32_t trace_cap, cudaStream_t s);
 cudaError_t launch_init(const EngineArgs& a, uint32_t max_n, cudaStream_t s);
 cudaError_t launch_engine(const EngineArgs& a, int grid, cudaStream_t s);

@@ -78,7 +78,17 @@ MODES = [
     # frequent narrow <-> wide transitions
     ("sub_resident_mixed", dict(mode=SUB, tile=128, narrow_max=300, narrow_edges=3000,
                                 unit_entries=512)),
+    # hybrid: bottom-up levels by the usual thresholds, on every level after the
+    # first, and alternating with top-down ones (every kind of hand-over)
+    ("sub_hybrid", dict(mode=SUB, bottom_up_alpha=14, bottom_up_beta=24)),
+    ("sub_hybrid_always", dict(mode=SUB, bottom_up_alpha=0xFFFFFFFF, bottom_up_beta=0xFFFFFFFF)),
+    ("sub_hybrid_alternate", dict(mode=SUB, bottom_up_alpha=0xFFFFFFFF, bottom_up_beta=0,
+                                  narrow_max=0, narrow_edges=0, unit_entries=256)),
+    ("sub_hybrid_scan", dict(mode=SUB, bottom_up_alpha=0xFFFFFFFF, bottom_up_beta=0, claim_scan=1,
+                             narrow_max=0, narrow_edges=0)),
 ]
+
+HYBRID = ("sub_hybrid", "sub_hybrid_always", "sub_hybrid_alternate", "sub_hybrid_scan")
 
 
 def _small_graphs():
@@ -138,6 +148,10 @@ def test_small_graphs_all_modes(small, mode_name, kw):
             assert st["levels"] == int(lev_o.max()) + 1, (name, s, st)
             nnz_c = int(g.degrees()[reached].sum())
             assert st["nnz_reached"] == nnz_c, (name, s, st)
+            if mode_name in HYBRID:
+                # bottom-up levels read rows until the first frontier entry:
+                # the entry counters of Claim 1 and E_adj do not apply
+                continue
             if kw.get("mode") == PLAIN:
                 assert st["entries_read"] == nnz_c and st["entries_unmasked"] == nnz_c
             else:
@@ -285,6 +299,54 @@ def test_batch_tune_picks_a_valid_set(small, tmp_path):
     plan.destroy()
 
 
+def _kinds(trace):
+    return {r["kind"] for r in trace}
+
+
+def test_hybrid_runs_bottom_up_only_where_allowed():
+    """Bottom-up levels appear on an undirected graph with ascending columns and
+    not on the same graph with shuffled columns, nor on a directed graph, nor
+    when path counts are requested; every result equals the oracle's."""
+    p = _params(bottom_up_alpha=0xFFFFFFFF, bottom_up_beta=0xFFFFFFFF)
+    g = synth.rmat(14, 16.0, seed=3)
+    s = int(np.argmax(g.degrees()))
+    G = abfs.graph_create(g.colptr, g.rowidx, directed=False)
+    level, parent, trace = abfs.run_trace(G, s, params=p)
+    assert "bottom_up" in _kinds(trace)
+    _check(g, s, level, parent, "sorted hybrid")
+    level, parent, sigma = abfs.run_counts(G, s, params=p)
+    _check(g, s, level, parent, "hybrid with counts")
+    assert np.array_equal(sigma.cpu().numpy().view(np.uint64), oracle.path_counts(g, s))
+    G.destroy()
+    # the same graph with each column's rows in a seeded random order
+    rng = np.random.default_rng(7)
+    rows = g.rowidx.copy()
+    for v in range(g.n):
+        a, b = int(g.colptr[v]), int(g.colptr[v + 1])
+        rows[a:b] = rng.permutation(rows[a:b])
+    H = abfs.graph_create(g.colptr, rows, directed=False)
+    level, parent, trace = abfs.run_trace(H, s, params=p)
+    assert "bottom_up" not in _kinds(trace) and "bu_prep" not in _kinds(trace)
+    _check(g, s, level, parent, "shuffled columns")
+    H.destroy()
+    d = synth.rgg_knn(1 << 14, 4, seed=4)
+    D = abfs.graph_create(d.colptr, d.rowidx, directed=True)
+    level, parent, trace = abfs.run_trace(D, 0, params=p)
+    assert "bottom_up" not in _kinds(trace)
+    _check(d, 0, level, parent, "directed hybrid")
+    D.destroy()
+
+
+def test_hybrid_parameter_rules():
+    G = abfs.graph_create(*(lambda g: (g.colptr, g.rowidx))(synth.er(100, 3.0, seed=1)))
+    for bad in (dict(mode=PLAIN, bottom_up_alpha=14),
+                dict(bottom_up_alpha=14, shrink_theta=0.5, shrink_max=1)):
+        with pytest.raises(abfs.AbfsError) as ei:
+            abfs.run(G, 0, params=_params(**bad))
+        assert ei.value.status == 1
+    G.destroy()
+
+
 def test_device_inputs_and_validation():
     g = synth.rmat(12, 8.0, seed=5)
     cp = torch.from_numpy(g.colptr.view(np.int32)).cuda()
@@ -311,7 +373,8 @@ def rmat22():
 def test_rmat22_16_sources(rmat22):
     g, G = rmat22
     srcs = synth.sources_with_degree(g, 16, seed=1)
-    for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, shrink_theta=0.6, shrink_max=1)):
+    for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, shrink_theta=0.6, shrink_max=1),
+               dict(mode=SUB, bottom_up_alpha=14, bottom_up_beta=24)):
         p = _params(**kw)
         for s in srcs[: (16 if kw == dict(mode=SUB) else 4)]:
             level, parent, st = abfs.run(G, int(s), params=p, stats=True)
