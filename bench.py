@@ -655,6 +655,38 @@ def main():
         cval = edges_per_step * c_steps / (cms * 1e-3) / 1e9
         line["comparator"] = {"name": "plain masked SpMSpV (same engine, multiply then mask)",
                               "value": cval, "unit": "GTEPS", "speedup_of_ours": value / cval}
+        # same GPU, same search, two variants beside the paper's method: the
+        # direction-optimising hybrid (bottom-up levels; identical results) and
+        # the shortest-path counts of the all-nonzero variant (abfs_run_counts)
+        def timed(fn, reps):
+            for s in srcs[:2]:
+                fn(int(s))
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(reps):
+                for s in srcs:
+                    fn(int(s))
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        hp = abfs.default_params(bottom_up_alpha=5, bottom_up_beta=24)
+        if not g.directed:
+            hms = timed(lambda s: abfs.run(G, s, level, parent, stream, hp), c_steps)
+            hval = edges_per_step / (hms * 1e-3) / 1e9
+            line["hybrid"] = {"name": "direction-optimising hybrid (bottom-up levels over sorted "
+                                      "columns, exact min-index parent; not the paper's method)",
+                              "params": {"bottom_up_alpha": 5, "bottom_up_beta": 24},
+                              "value": hval, "unit": "GTEPS", "per_bfs_ms": hms / nsrc,
+                              "speedup_vs_submatrix": hval / value}
+        sigma = torch.empty(n, dtype=torch.int64, device="cuda")
+        cms2 = timed(lambda s: abfs.run_counts(G, s, level, parent, sigma, stream, params), c_steps)
+        line["path_counts"] = {"name": "abfs_run_counts: shortest-path counts mod 2^64 (all-nonzero "
+                                       "variant, arithmetic semiring)",
+                               "value": edges_per_step / (cms2 * 1e-3) / 1e9, "unit": "GTEPS",
+                               "per_bfs_ms": cms2 / nsrc,
+                               "time_vs_abfs_run": cms2 / nsrc / float(per_bfs_ms.mean())}
+        del sigma
         # batched: 64 sources in one persistent launch (CUDA graph replay)
         if args.workload == "rmat22":
             bs = synth.sources_with_degree(g, 64, seed=2)

@@ -1067,46 +1067,57 @@ __device__ ABFS_NOINLINE void unit_plain_mask(const Inst& I, InstCtl* ctl, const
 }
 
 // Vertices per extraction unit: one bitmap word per thread.
-constexpr uint32_t kExtractWords = kThreads;
+constexpr uint32_t kExtractWarpWords = 8;                       // bitmap words per warp in a unit
+constexpr uint32_t kExtractWords = kWarps * kExtractWarpWords;  // bitmap words per unit
 
 // Extraction after a level k whose claims were reductions: the vertices of
 // level k+1 (V_{k+1} minus V_{k+2} in the paper's terms) are those outside the
 // test bitmap (not reached by level k) whose parent the level set.  Unit u
-// covers bitmap words [u*kExtractWords, ...); each warp reads the parents of
-// its 32 words' candidates (coalesced, a word at a time), hands the new
-// vertices to the frontier blocks of level k+1 and adds them to the write
-// bitmap (one store per word; the level's frontier marks are already there).
+// covers bitmap words [u*kExtractWords, ...), eight per warp; the warp loads
+// the parents of all its candidates first (coalesced, one word per load, all
+// eight in flight), then hands the new vertices to the frontier blocks of level
+// k+1 and adds them to the write bitmap (one store per word; the level's
+// frontier marks are already there).
 __device__ ABFS_NOINLINE void unit_extract(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                              uint32_t k, uint32_t u) {
     const uint32_t p = k & 1, pn = p ^ 1;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t mat, mat_next;
     level_mats(ctl, k, mat, mat_next);
-    const uint32_t w0 = u * kExtractWords + warp * 32;
+    const uint32_t w0 = u * kExtractWords + warp * kExtractWarpWords;
     const uint32_t wi = w0 + lane;
+    const bool own = lane < kExtractWarpWords && wi < I.nwords;
     uint32_t cand = 0, wb = 0;
-    if (wi < I.nwords) {
+    if (own) {
         cand = ~ld_l2(I.bm[p] + wi);
         wb = ld_l2(I.bm[pn] + wi);
         // no vertices past n in the last word
         if (wi == I.nwords - 1 && (I.n & 31)) cand &= (1u << (I.n & 31)) - 1u;
     }
+    uint32_t par[kExtractWarpWords];
+#pragma unroll
+    for (uint32_t q = 0; q < kExtractWarpWords; ++q) {
+        const uint32_t c = __shfl_sync(0xFFFFFFFFu, cand, q);
+        par[q] = ((c >> lane) & 1u) ? ld_l2(I.parent + (w0 + q) * 32 + lane) : kUnset;
+    }
     uint32_t fresh = 0;  // lane q: the new vertices of word w0 + q
     uint32_t wc = sm.wcnt[warp];
-    for (uint32_t q = 0; q < 32; ++q) {
-        const uint32_t c = __shfl_sync(0xFFFFFFFFu, cand, q);
-        if (!c) continue;
-        const uint32_t v = (w0 + q) * 32 + lane;
-        const bool want = ((c >> lane) & 1u) && ld_l2(I.parent + v) != kUnset;
+#pragma unroll
+    for (uint32_t q = 0; q < kExtractWarpWords; ++q) {
+        const bool want = par[q] != kUnset;
         const uint32_t bits = __ballot_sync(0xFFFFFFFFu, want);
+        if (!bits) continue;
         if (lane == q) fresh = bits;
+        const uint32_t v = (w0 + q) * 32 + lane;
         if (want) I.level[v] = (int32_t)(k + 1);
         stage_warp(want, v, sm, wc);
         if (wc > (uint32_t)(kWarpBuf - 32)) warp_flush(sm, I, ctl, P, pn, mat_next, wc);
     }
-    if (fresh) I.bm[pn][wi] = wb | fresh;
-    // hybrid: the frontier bitmap of level k+1, in case it runs bottom-up
-    if (P.bu_alpha && I.bu_ok && wi < I.nwords) I.fbm[pn][wi] = fresh;
+    if (own) {
+        if (fresh) I.bm[pn][wi] = wb | fresh;
+        // hybrid: the frontier bitmap of level k+1, in case it runs bottom-up
+        if (P.bu_alpha && I.bu_ok) I.fbm[pn][wi] = fresh;
+    }
     if (lane == 0) sm.wcnt[warp] = wc;
     __syncwarp();
     cta_flush(sm, I, ctl, P, pn, mat_next);
@@ -2233,6 +2244,16 @@ static cudaError_t set_smem_attr() {
     cudaError_t e = cudaFuncSetAttribute(engine_kernel<MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(Smem));
+#if ABFS_CARVEOUT
+    // the smallest shared-memory split that still holds kMinCtas CTAs leaves
+    // the rest of the SM's on-chip memory to L1, where the visited-bitmap
+    // words are cached
+    if (e == cudaSuccess) {
+        const int pct = (int)((kMinCtas * (sizeof(Smem) + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
+        e = cudaFuncSetAttribute(engine_kernel<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 pct > 100 ? 100 : pct);
+    }
+#endif
     if (e == cudaSuccess) done = true;
     return e;
 }

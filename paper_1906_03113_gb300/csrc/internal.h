@@ -36,6 +36,11 @@ constexpr int kIlp = ABFS_ILP;
 #define ABFS_ILP_SCAN 4
 #endif
 constexpr int kIlpScan = ABFS_ILP_SCAN;
+// Prefer the smallest shared-memory carveout that holds the resident CTAs (1)
+// or leave the split to the driver (0).
+#ifndef ABFS_CARVEOUT
+#define ABFS_CARVEOUT 1
+#endif
 // Per-warp staging buffer for newly reached vertices.  A warp writes its
 // buffer out as one frontier block once a further expand step (32 * kIlp
 // appends) might not fit; at the end of a unit the leftovers of all warps
