@@ -594,6 +594,12 @@ def main():
     hbm, peak_kind = _peaks()
     mean_t = float(per_bfs_ms.mean()) * 1e-3
     achieved = float(b_alg.mean()) / mean_t / 1e9
+    # the on-chip ceiling: every stored entry of a reached column costs one
+    # random visited-bitmap load, every entry that passes the mask one random
+    # reduction, both served by L2 (rates measured on this GPU, now)
+    cal = abfs.calibrate(22)
+    l2_bound_s = float(nnz_c.mean()) / (cal["load_gops"] * 1e9) + float(e_adj.mean()) / (
+        cal["red_gops"] * 1e9)
     line = {
         "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
@@ -611,7 +617,11 @@ def main():
                      "kernel": "engine_kernel<0> (one launch per BFS, with 3 small init kernels)",
                      "bytes_per_bfs": float(b_alg.mean()),
                      "bytes_formula": "4*E_adj + 24*n_c",
-                     "full_column_gbs": float(b_cols.mean()) / mean_t / 1e9},
+                     "full_column_gbs": float(b_cols.mean()) / mean_t / 1e9,
+                     "l2": {"random_load_gops": cal["load_gops"], "random_red_gops": cal["red_gops"],
+                            "formula": "nnz_c / load rate + E_adj / red rate",
+                            "bound_ms_per_bfs": l2_bound_s * 1e3,
+                            "frac": l2_bound_s / mean_t}},
         "gpu_launches": 4 * nsrc * args.steps,
         "clocks": clk,
         "per_bfs_ms": float(per_bfs_ms.mean()),

@@ -365,6 +365,24 @@ int abfs_run_static(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, 
 int abfs_set_allocator(void* (*alloc)(size_t bytes, void* ctx), void (*free_fn)(void* ptr, void* ctx),
                        void* ctx);
 
+/* On-chip ceilings of the expand step, measured on the current device. */
+typedef struct {
+    uint32_t words;     /* array size in 32-bit words (2^words_log2) */
+    uint32_t reserved;
+    uint64_t ops;       /* operations per measurement */
+    double red_gops;    /* random 32-bit red.min into the array, 10^9 per second */
+    double load_gops;   /* random 32-bit loads from the array through L2, 10^9 per second */
+} abfs_calibration;
+
+/*
+ * Times random 32-bit reductions and random 32-bit L2 loads over an array of
+ * 2^words_log2 words (10..26), the two accesses each column entry costs (the
+ * visited-bitmap test and the (min, index) claim) when their targets sit in
+ * L2.  Allocates and frees 4 * 2^words_log2 bytes; synchronises `stream`.
+ * Diagnostics only: no search uses it.
+ */
+int abfs_calibrate(uint32_t words_log2, abfs_calibration* out, abfs_stream_t stream);
+
 /* Text of the last CUDA runtime error seen by this thread ("" if none). */
 const char* abfs_last_cuda_error(void);
 

@@ -23,6 +23,7 @@ from .binding import (  # noqa: F401
     load,
     run,
     run_counts,
+    calibrate,
     run_batch,
     run_host,
     run_trace,

@@ -113,6 +113,11 @@ class AbfsError(RuntimeError):
         super().__init__(f"{where}: {msg}{extra} [status {status}]")
 
 
+class Calibration(ctypes.Structure):
+    _fields_ = [("words", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("ops", ctypes.c_uint64),
+                ("red_gops", ctypes.c_double), ("load_gops", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -145,6 +150,7 @@ def load():
         "abfs_graph_footprint": ([vp, P(Params), P(ctypes.c_size_t)], c_int),
         "abfs_run": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
         "abfs_run_counts": ([vp, u32, vp, vp, vp, vp, P(Params), P(Stats)], c_int),
+        "abfs_calibrate": ([u32, P(Calibration), vp], c_int),
         "abfs_run_host": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
         "abfs_run_trace": ([vp, u32, vp, vp, vp, P(Params), vp, u32, P(u32)], c_int),
         "abfs_run_batch": ([P(vp), P(u32), u32, P(vp), P(vp), vp, P(Params), P(i32)], c_int),
@@ -307,6 +313,14 @@ def run_counts(g: Graph, source: int, level=None, parent=None, sigma=None, strea
                                 ctypes.byref(st) if st else None)
     _check(rc, "abfs_run_counts")
     return (level, parent, sigma, st.as_dict()) if stats else (level, parent, sigma)
+
+
+def calibrate(words_log2: int = 22, stream=None) -> dict:
+    """abfs_calibrate: random L2 load and red.min rates (10^9/s) over 2^words_log2 words."""
+    c = Calibration()
+    _check(load().abfs_calibrate(int(words_log2), ctypes.byref(c), _stream_ptr(stream)),
+           "abfs_calibrate")
+    return {"words": c.words, "ops": c.ops, "red_gops": c.red_gops, "load_gops": c.load_gops}
 
 
 TRACE_KINDS = {0: "level", 1: "plain_mult", 2: "plain_mask", 3: "shrink", 4: "init",

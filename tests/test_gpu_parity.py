@@ -347,6 +347,14 @@ def test_hybrid_parameter_rules():
     G.destroy()
 
 
+def test_calibrate_reports_rates():
+    c = abfs.calibrate(16)
+    assert c["words"] == 1 << 16 and c["ops"] > 0
+    assert c["red_gops"] > 1.0 and c["load_gops"] > 1.0
+    with pytest.raises(abfs.AbfsError):
+        abfs.calibrate(40)
+
+
 def test_device_inputs_and_validation():
     g = synth.rmat(12, 8.0, seed=5)
     cp = torch.from_numpy(g.colptr.view(np.int32)).cuda()
