@@ -57,6 +57,9 @@ namespace abfs {
 // register allocation, so the cold paths' state does not push the hot loop
 // into spills.  -DABFS_INLINE_ALL inlines them instead.
 // Longest sleep of an idle CTA between polls for work.
+#ifndef ABFS_UNIT_CEIL
+#define ABFS_UNIT_CEIL 1
+#endif
 #ifndef ABFS_IDLE_BACKOFF_NS
 #define ABFS_IDLE_BACKOFF_NS 2048
 #endif
@@ -1067,26 +1070,27 @@ __device__ ABFS_NOINLINE void unit_plain_mask(const Inst& I, InstCtl* ctl, const
 }
 
 // Vertices per extraction unit: one bitmap word per thread.
-constexpr uint32_t kExtractWarpWords = 8;                       // bitmap words per warp in a unit
-constexpr uint32_t kExtractWords = kWarps * kExtractWarpWords;  // bitmap words per unit
+// Bitmap-word phases (extraction, frontier bitmap, bottom-up levels) work in
+// chunks of 8 words, one chunk per warp at a time; a unit is a run of chunks
+// (nitems per unit, chosen by the advancing CTA so a phase makes about two
+// units per CTA), which keeps the per-unit costs (take, flush, count-down) to
+// two per CTA whatever the size of the graph.
+constexpr uint32_t kChunkWords = 8;
 
 // Extraction after a level k whose claims were reductions: the vertices of
 // level k+1 (V_{k+1} minus V_{k+2} in the paper's terms) are those outside the
-// test bitmap (not reached by level k) whose parent the level set.  Unit u
-// covers bitmap words [u*kExtractWords, ...), eight per warp; the warp loads
-// the parents of all its candidates first (coalesced, one word per load, all
-// eight in flight), then hands the new vertices to the frontier blocks of level
-// k+1 and adds them to the write bitmap (one store per word; the level's
-// frontier marks are already there).
-__device__ ABFS_NOINLINE void unit_extract(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                             uint32_t k, uint32_t u) {
+// test bitmap (not reached by level k) whose parent the level set.  A warp
+// loads the parents of all candidates of its chunk first (coalesced, one word
+// per load, all eight in flight), then hands the new vertices to the frontier
+// blocks of level k+1 and adds them to the write bitmap (one store per word;
+// the level's frontier marks are already there).
+__device__ __forceinline__ void extract_chunk(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                              Smem& sm, uint32_t k, uint32_t w0, uint32_t mat_next,
+                                              uint32_t& wc) {
     const uint32_t p = k & 1, pn = p ^ 1;
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t mat, mat_next;
-    level_mats(ctl, k, mat, mat_next);
-    const uint32_t w0 = u * kExtractWords + warp * kExtractWarpWords;
+    const uint32_t lane = threadIdx.x & 31;
     const uint32_t wi = w0 + lane;
-    const bool own = lane < kExtractWarpWords && wi < I.nwords;
+    const bool own = lane < kChunkWords && wi < I.nwords;
     uint32_t cand = 0, wb = 0;
     if (own) {
         cand = ~ld_l2(I.bm[p] + wi);
@@ -1094,16 +1098,15 @@ __device__ ABFS_NOINLINE void unit_extract(const Inst& I, InstCtl* ctl, const En
         // no vertices past n in the last word
         if (wi == I.nwords - 1 && (I.n & 31)) cand &= (1u << (I.n & 31)) - 1u;
     }
-    uint32_t par[kExtractWarpWords];
+    uint32_t par[kChunkWords];
 #pragma unroll
-    for (uint32_t q = 0; q < kExtractWarpWords; ++q) {
+    for (uint32_t q = 0; q < kChunkWords; ++q) {
         const uint32_t c = __shfl_sync(0xFFFFFFFFu, cand, q);
         par[q] = ((c >> lane) & 1u) ? ld_l2(I.parent + (w0 + q) * 32 + lane) : kUnset;
     }
     uint32_t fresh = 0;  // lane q: the new vertices of word w0 + q
-    uint32_t wc = sm.wcnt[warp];
 #pragma unroll
-    for (uint32_t q = 0; q < kExtractWarpWords; ++q) {
+    for (uint32_t q = 0; q < kChunkWords; ++q) {
         const bool want = par[q] != kUnset;
         const uint32_t bits = __ballot_sync(0xFFFFFFFFu, want);
         if (!bits) continue;
@@ -1118,9 +1121,22 @@ __device__ ABFS_NOINLINE void unit_extract(const Inst& I, InstCtl* ctl, const En
         // hybrid: the frontier bitmap of level k+1, in case it runs bottom-up
         if (P.bu_alpha && I.bu_ok) I.fbm[pn][wi] = fresh;
     }
-    if (lane == 0) sm.wcnt[warp] = wc;
+}
+
+// Unit u of an extraction: chunks [u*per, (u+1)*per).
+__device__ ABFS_NOINLINE void unit_extract(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
+                             uint32_t k, uint32_t u, uint32_t per) {
+    const uint32_t warp = threadIdx.x >> 5;
+    uint32_t mat, mat_next;
+    level_mats(ctl, k, mat, mat_next);
+    const uint32_t chunks = (I.nwords + kChunkWords - 1) / kChunkWords;
+    const uint32_t c1 = min(chunks, (u + 1) * per);
+    uint32_t wc = sm.wcnt[warp];
+    for (uint32_t c = u * per + warp; c < c1; c += kWarps)
+        extract_chunk(I, ctl, P, sm, k, c * kChunkWords, mat_next, wc);
+    if ((threadIdx.x & 31) == 0) sm.wcnt[warp] = wc;
     __syncwarp();
-    cta_flush(sm, I, ctl, P, pn, mat_next);
+    cta_flush(sm, I, ctl, P, (k & 1) ^ 1, mat_next);
 }
 
 // ---------------------------------------------------------------------------
@@ -1135,45 +1151,40 @@ __device__ ABFS_NOINLINE void unit_extract(const Inst& I, InstCtl* ctl, const En
 // only the order of evaluation changes.  The frontier of level k is read from
 // a bitmap (fbm[k & 1]).
 
-constexpr uint32_t kBuWarpWords = 8;                  // bitmap words per warp in a unit
-constexpr uint32_t kBuWords = kWarps * kBuWarpWords;  // bitmap words per unit
-constexpr uint32_t kBuLaneBatches = 4;                // lane-serial scan: 4 batches of 4 entries
+constexpr uint32_t kBuLaneBatches = 4;  // lane-serial scan: 4 batches of 4 entries
 
 // Frontier bitmap of level k after a top-down level: at the start of level k
 // the test bitmap holds the levels <= k and the write bitmap the levels < k.
-__device__ ABFS_NOINLINE void unit_bu_prep(const Inst& I, uint32_t k, uint32_t u) {
+// Unit u: chunks [u*per, (u+1)*per).
+__device__ ABFS_NOINLINE void unit_bu_prep(const Inst& I, uint32_t k, uint32_t u, uint32_t per) {
     const uint32_t p = k & 1;
-    const uint32_t w1 = min(I.nwords, (u + 1) * kExtractWords);
-    for (uint32_t w = u * kExtractWords + threadIdx.x; w < w1; w += kThreads)
+    const uint32_t w1 = min(I.nwords, (u + 1) * per * kChunkWords);
+    for (uint32_t w = u * per * kChunkWords + threadIdx.x; w < w1; w += kThreads)
         I.fbm[p][w] = ld_l2(I.bm[p] + w) & ~ld_l2(I.bm[p ^ 1] + w);
 }
 
-// Bottom-up level k over bitmap words [u*kBuWords, ...): each lane takes one
-// unvisited vertex of a word and scans the first entries of its column itself,
-// four at a time; columns still unresolved after that are scanned by the whole
-// warp, 32 entries at a time.  Found vertices get level k+1 and their parent,
-// go to the frontier blocks of level k+1, the write bitmap (one store per word:
+// Bottom-up level k over the chunk at word w0: each lane takes one unvisited
+// vertex of a word and scans the first entries of its column itself, four at
+// a time; columns still unresolved after that are scanned by the whole warp,
+// 32 entries at a time.  Found vertices get level k+1 and their parent, go to
+// the frontier blocks of level k+1, the write bitmap (one store per word:
 // test | new = the levels <= k+1) and the next frontier bitmap.
-__device__ ABFS_NOINLINE void unit_bottom_up(const Inst& I, InstCtl* ctl, const EngineParams& P,
-                                             Smem& sm, uint32_t k, uint32_t u) {
+__device__ __forceinline__ void bu_chunk(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                         Smem& sm, uint32_t k, uint32_t w0, uint32_t mat_next,
+                                         uint32_t& wc, Tally& t) {
     const uint32_t p = k & 1, pn = p ^ 1;
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t mat, mat_next;
-    level_mats(ctl, k, mat, mat_next);
+    const uint32_t lane = threadIdx.x & 31;
     const uint32_t* fbm = I.fbm[p];
-    const uint32_t w0 = u * kBuWords + warp * kBuWarpWords;
     const uint32_t wi = w0 + lane;
-    const bool own = lane < kBuWarpWords && wi < I.nwords;
+    const bool own = lane < kChunkWords && wi < I.nwords;
     uint32_t tb = 0, cand = 0;
     if (own) {
         tb = ld_frozen(I.bm[p] + wi);
         cand = ~tb;
         if (wi == I.nwords - 1 && (I.n & 31)) cand &= (1u << (I.n & 31)) - 1u;
     }
-    Tally t;
     uint32_t fresh = 0;  // lane q: the new vertices of word w0 + q
-    uint32_t wc = sm.wcnt[warp];
-    for (uint32_t q = 0; q < kBuWarpWords; ++q) {
+    for (uint32_t q = 0; q < kChunkWords; ++q) {
         const uint32_t c = __shfl_sync(0xFFFFFFFFu, cand, q);
         if (!c) continue;
         const uint32_t v = (w0 + q) * 32 + lane;
@@ -1233,10 +1244,24 @@ __device__ ABFS_NOINLINE void unit_bottom_up(const Inst& I, InstCtl* ctl, const 
         I.bm[pn][wi] = tb | fresh;
         I.fbm[pn][wi] = fresh;
     }
-    if (lane == 0) sm.wcnt[warp] = wc;
+}
+
+// Unit u of a bottom-up level: chunks [u*per, (u+1)*per).
+__device__ ABFS_NOINLINE void unit_bottom_up(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                             Smem& sm, uint32_t k, uint32_t u, uint32_t per) {
+    const uint32_t warp = threadIdx.x >> 5;
+    uint32_t mat, mat_next;
+    level_mats(ctl, k, mat, mat_next);
+    const uint32_t chunks = (I.nwords + kChunkWords - 1) / kChunkWords;
+    const uint32_t c1 = min(chunks, (u + 1) * per);
+    Tally t;
+    uint32_t wc = sm.wcnt[warp];
+    for (uint32_t c = u * per + warp; c < c1; c += kWarps)
+        bu_chunk(I, ctl, P, sm, k, c * kChunkWords, mat_next, wc, t);
+    if ((threadIdx.x & 31) == 0) sm.wcnt[warp] = wc;
     __syncwarp();
     tally_flush(sm, t);
-    cta_flush(sm, I, ctl, P, pn, mat_next);
+    cta_flush(sm, I, ctl, P, (k & 1) ^ 1, mat_next);
 }
 
 // Shrink: compacts the unvisited columns among vertices
@@ -1357,11 +1382,11 @@ __device__ void run_unit(const Inst& I, InstCtl* ctl, const EngineParams& P, Sme
     } else if (kind == kPhPlainMask) {
         unit_plain_mask(I, ctl, P, sm, k, unit, nitems);
     } else if (kind == kPhExtract) {
-        unit_extract(I, ctl, P, sm, k, unit);
+        unit_extract(I, ctl, P, sm, k, unit, nitems);
     } else if (kind == kPhBuPrep) {
-        unit_bu_prep(I, k, unit);
+        unit_bu_prep(I, k, unit, nitems);
     } else if (MODE == kModeSub && kind == kPhBottomUp) {
-        unit_bottom_up(I, ctl, P, sm, k, unit);
+        unit_bottom_up(I, ctl, P, sm, k, unit, nitems);
     } else if (MODE == kModeSub && kind == kPhLevelScan) {
         unit_level<MODE, kVarScan>(I, ctl, P, sm, k, unit, nitems);
     } else {
@@ -1811,11 +1836,12 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
         } else if (nkind == kPhPlainMask) {
             units = (ni + P.tile - 1) / P.tile;
             alone = ni <= P.narrow_max;
-        } else if (nkind == kPhExtract || nkind == kPhBuPrep) {
-            units = (I.nwords + kExtractWords - 1) / kExtractWords;
-            alone = units <= 1;
-        } else if (nkind == kPhBottomUp) {
-            units = (I.nwords + kBuWords - 1) / kBuWords;
+        } else if (nkind == kPhExtract || nkind == kPhBuPrep || nkind == kPhBottomUp) {
+            // runs of 8-word chunks, about two units per CTA (ni = chunks per unit)
+            const uint32_t chunks = (I.nwords + kChunkWords - 1) / kChunkWords;
+            const uint32_t two = 2u * gridDim.x;
+            ni = max((chunks + two - 1) / two, (uint32_t)kWarps);
+            units = (chunks + ni - 1) / ni;
             alone = units <= 1;
         } else {
             // a level (or the comparator's multiply) over the frontier of level nk;
@@ -1823,7 +1849,14 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
             ne = ld_relaxed64(&ctl->bctr[nk & 1]) >> kBlockBits;
             nf = ld_relaxed(&ctl->fcnt[nk & 1]);
             const unsigned long long mmax = kUnitMax / P.unit;
+#if ABFS_UNIT_CEIL
+            // at most two units per CTA: a third round for a few CTAs would
+            // stretch the level by half
+            const unsigned long long per2 = (unsigned long long)P.unit * 2ull * gridDim.x;
+            unsigned long long m = (ne + per2 - 1) / per2;
+#else
             unsigned long long m = ne / ((unsigned long long)P.unit * 2ull * gridDim.x);
+#endif
             m = m < 1ull ? 1ull : (m > mmax ? mmax : m);
             ni = (uint32_t)m;
             units = (uint32_t)((ne + P.unit * m - 1) / (P.unit * m));
