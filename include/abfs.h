@@ -101,8 +101,8 @@ typedef struct {
                                  yet), until the frontier's size n_f satisfies
                                  n_f * beta < n.  Results are identical.  Applies to
                                  undirected graphs whose columns ascend (checked at
-                                 abfs_graph_create) in abfs_run / abfs_run_host; other
-                                 searches stay top-down.  Submatrix mode without physical
+                                 abfs_graph_create) in abfs_run, abfs_run_host and
+                                 batches; path counts and serving stay top-down.  Submatrix mode without physical
                                  shrink only (else ABFS_ERR_INVALID_ARG). */
     uint32_t bottom_up_beta;  /* see bottom_up_alpha */
 } abfs_params;

@@ -333,7 +333,10 @@ void free_workspace(Workspace& w) {
 
 Inst make_inst(const abfs_graph_s* g, char* base, const Layout& L, uint32_t src, int32_t* level,
                int32_t* parent) {
-    return make_inst_raw(g->d_colptr, g->d_rowidx, g->n, base, L, src, level, parent);
+    Inst I = make_inst_raw(g->d_colptr, g->d_rowidx, g->n, base, L, src, level, parent);
+    // the hybrid's bottom-up levels need a symmetric pattern and ascending columns
+    I.bu_ok = (!g->directed && g->sorted) ? 1u : 0u;
+    return I;
 }
 
 // Ensures g->ws fits params p (reallocating after the previous use finished).

@@ -241,7 +241,9 @@ def test_batch_alone_equals_mix(small):
             graphs.append(dev[nm])
             srcs.append(s)
             hosts.append(gs[nm])
-    for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, shrink_theta=0.4, shrink_max=2)):
+    for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, shrink_theta=0.4, shrink_max=2),
+               dict(mode=SUB, bottom_up_alpha=5, bottom_up_beta=24),
+               dict(mode=SUB, bottom_up_alpha=0xFFFFFFFF, bottom_up_beta=0)):
         p = _params(**kw)
         levels, parents, st = abfs.run_batch(graphs, srcs, params=p)
         torch.cuda.synchronize()
