@@ -276,8 +276,9 @@ def bench_batch(args, ws, rank, local, torch, abfs, dist):
     # parameters for the whole batch from the batch autotuner (outside the timing)
     tuned, tuned_ms = abfs.batch_tune(qg, qs)
 
-    def batched_vs_single(gs, ss, clocks=None):
-        plan = abfs.BatchPlan(gs, ss, params=tuned)
+    def batched_vs_single(gs, ss, clocks=None, params=None):
+        params = tuned if params is None else params
+        plan = abfs.BatchPlan(gs, ss, params=params)
         for _ in range(max(args.warmup, 3)):
             plan.launch(stream)
         torch.cuda.synchronize()
@@ -296,7 +297,7 @@ def bench_batch(args, ws, rank, local, torch, abfs, dist):
         # the same queries, one launch each
         a.record(stream)
         for G, s_ in zip(gs, ss):
-            abfs.run(G, s_, lv[:G.n], pv[:G.n], stream)
+            abfs.run(G, s_, lv[:G.n], pv[:G.n], stream, params)
         b.record(stream)
         torch.cuda.synchronize()
         return bms, a.elapsed_time(b), clk
@@ -310,6 +311,13 @@ def bench_batch(args, ws, rank, local, torch, abfs, dist):
                        "batched_gteps": e / (bms * 1e-3) / 1e9,
                        "single_query_gteps": e / (sms * 1e-3) / 1e9,
                        "speedup_vs_single": sms / bms}
+    # the direction-optimising hybrid (not the paper's method) on the same queries
+    hp = abfs.default_params(bottom_up_alpha=5, bottom_up_beta=24)
+    hbms, hsms, _ = batched_vs_single(qg, qs, params=hp)
+    hybrid = {"name": "direction-optimising hybrid, bottom_up_alpha 5, bottom_up_beta 24 "
+                      "(not the paper's method)",
+              "batched_ms": hbms, "batched_gteps": total_edges / (hbms * 1e-3) / 1e9,
+              "single_query_ms": hsms, "speedup_vs_single": hsms / hbms}
     nq = len(qg)
     value, _ = job_throughput(total_edges, batch_ms, dist, "cuda")
     line = {
@@ -327,6 +335,7 @@ def bench_batch(args, ws, rank, local, torch, abfs, dist):
                     "single_query_gteps": total_edges / (single_ms * 1e-3) / 1e9,
                     "speedup_vs_single": single_ms / batch_ms, "parts": parts,
                     "tuned_params": tuned.as_dict(), "tuner_ms": tuned_ms},
+        "hybrid": hybrid,
         "gpu_launches": 3 * steps, "clocks": clk,
     }
     if rank == 0:
