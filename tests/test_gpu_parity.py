@@ -111,6 +111,9 @@ def _small_graphs():
         "two_components": synth.from_arcs(100, list(range(49)) + list(range(50, 99)),
                                           list(range(1, 50)) + list(range(51, 100)), directed=False),
         "no_edges": synth.from_arcs(77, [], [], directed=False),
+        # one vertex; a path ending just past a bitmap word (ragged last word)
+        "one_vertex": synth.from_arcs(1, [], [], directed=False),
+        "path_33": synth.from_arcs(33, list(range(32)), list(range(1, 33)), directed=False),
     }
 
 
