@@ -1375,6 +1375,8 @@ __device__ void run_unit(const Inst& I, InstCtl* ctl, const EngineParams& P, Sme
                          uint32_t kind, uint32_t k, uint32_t unit, uint32_t nitems) {
     if (kind == kPhInit) {
         unit_init(I, P, unit);
+    } else if (kind == kPhStart) {
+        // nothing: the CTA that completes it advances into level 0
     } else if (kind == kPhShrink) {
         // k = level just completed; its write bitmap holds every vertex reached so far
         const uint32_t src_mat = ld_relaxed(&ctl->mat_cur);
@@ -1703,6 +1705,10 @@ __device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const Eng
         st_relaxed64(&ctl->bctr[0], ((unsigned long long)w << kBlockBits) | 1ull);
         st_relaxed(&ctl->fcnt[0], 1u);
         st_relaxed(&ctl->reached, 1u);
+        nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
+        nk = 0;
+    } else if (kind == kPhStart) {
+        // the frontier of level 0 (the source) was set up before the launch
         nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
         nk = 0;
     } else if (kind == kPhLevelScan) {
@@ -2185,13 +2191,14 @@ __global__ void init_source_kernel(EngineArgs a) {
     ctl->mat_cur = 0;
     ctl->mat_prev = 0;
     ctl->mat_switch = 0;
-    const uint32_t units = (w + P.unit - 1) / P.unit;
-    ctl->kind[0] = (P.mode == kModePlain) ? kPhPlainMult : kPhLevel;
+    // the first CTA to arrive advances into level 0, which then starts a
+    // resident run when it is small (the usual case) instead of a grid phase
+    ctl->kind[0] = kPhStart;
     ctl->plevel[0] = 0;
-    ctl->nitems[0] = 1;  // one granule per unit
-    ctl->pending[0] = units;
+    ctl->nitems[0] = 0;
+    ctl->pending[0] = 1;
     ctl->epoch = 0;
-    ctl->desc[0] = (0ull << 32) | units;
+    ctl->desc[0] = (0ull << 32) | 1ull;
     ctl->desc[1] = ~0ull;
     ctl->grab = 0ull;
     ctl->status = kRunning;

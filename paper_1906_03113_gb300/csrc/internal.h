@@ -76,6 +76,7 @@ enum PhaseKind : uint32_t {
     kPhExtract = 6,    // the vertices a kPhLevelScan level reached, read off the bitmaps
     kPhBuPrep = 7,     // hybrid: the frontier bitmap of a bottom-up level that follows a top-down one
     kPhBottomUp = 8,   // hybrid: unvisited vertices scan their sorted columns for a frontier entry
+    kPhStart = 9,      // one empty unit: its CTA advances into level 0 (a resident run if small)
 };
 
 enum InstStatus : uint32_t { kIdle = 0, kRunning = 1, kDone = 2, kFailed = 3 };
