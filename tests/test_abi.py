@@ -59,6 +59,11 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
                                  ctypes.byref(out)) == binding.ERR_NOT_SYMMETRIC
     # null handles
     assert lib.abfs_run(None, 0, None, None, None, None, None) == binding.ERR_INVALID_ARG
+    assert lib.abfs_run_counts(None, 0, None, None, None, None, None, None) == binding.ERR_INVALID_ARG
+    cal = binding.Calibration()
+    assert lib.abfs_calibrate(9, ctypes.byref(cal), None) == binding.ERR_INVALID_ARG
+    assert lib.abfs_calibrate(27, ctypes.byref(cal), None) == binding.ERR_INVALID_ARG
+    assert lib.abfs_calibrate(16, None, None) == binding.ERR_INVALID_ARG
     assert lib.abfs_graph_destroy(None) == binding.ERR_INVALID_ARG
     assert lib.abfs_batch_destroy(None) == binding.ERR_INVALID_ARG
 
@@ -79,10 +84,14 @@ def test_parameter_validation(lib):
     for kw in (dict(tile=32), dict(tile=1024), dict(unit_entries=256), dict(unit_entries=32768),
                dict(mode=abfs.MODE_PLAIN), dict(ctas_per_sm=1), dict(shrink_theta=0.5, shrink_max=2),
                dict(narrow_resident=0), dict(claim_scan=0), dict(claim_scan=1),
-               dict(narrow_max=0, narrow_edges=0)):
+               dict(narrow_max=0, narrow_edges=0), dict(bottom_up_alpha=5, bottom_up_beta=24),
+               dict(bottom_up_alpha=0xFFFFFFFF, bottom_up_beta=0)):
         assert check(**kw) == ok, kw
     for kw in (dict(tile=16), dict(tile=1056), dict(tile=100), dict(unit_entries=128),
                dict(unit_entries=768), dict(unit_entries=65536), dict(mode=2), dict(ctas_per_sm=0),
                dict(ctas_per_sm=9), dict(shrink_theta=-0.1), dict(shrink_theta=1.5),
-               dict(timeout_ms=0), dict(narrow_resident=2)):
+               dict(timeout_ms=0), dict(narrow_resident=2),
+               # the hybrid reads the input columns: submatrix mode without shrink only
+               dict(mode=abfs.MODE_PLAIN, bottom_up_alpha=5),
+               dict(bottom_up_alpha=5, shrink_theta=0.5, shrink_max=1)):
         assert check(**kw) == bad, kw

@@ -405,6 +405,27 @@ def test_rmat22_batch_64_sources(rmat22):
         _check(g, int(srcs[i]), levels[i], parents[i], f"rmat22 batch {i}")
 
 
+def test_batch_512_graphs_as_benchmarked():
+    """The benchmark's 512-graph batch (seeded ER/R-MAT, n in [2^10, 2^18]) in one
+    persistent launch with the batch autotuner's parameters: every status is OK
+    and a seeded sample of 48 searches equals the oracle bit for bit."""
+    specs = synth.batch_specs(512, seed=1)
+    hosts = [synth.make_batch_graph(sp) for sp in specs]
+    graphs = [abfs.graph_create(h.colptr, h.rowidx, directed=False) for h in hosts]
+    srcs = [int(synth.sources_with_degree(h, 1, seed=1 + i)[0]) if (h.degrees() > 0).any() else 0
+            for i, h in enumerate(hosts)]
+    for p in (abfs.batch_tune(graphs, srcs)[0], _params(bottom_up_alpha=5, bottom_up_beta=24)):
+        plan = abfs.BatchPlan(graphs, srcs, params=p)
+        plan.launch()
+        assert plan.status() == [0] * len(graphs)
+        rng = np.random.default_rng(11)
+        for i in rng.choice(len(graphs), size=48, replace=False).tolist():
+            _check(hosts[i], srcs[i], plan.levels[i], plan.parents[i], f"batch512 graph {i}")
+        plan.destroy()
+    for G in graphs:
+        G.destroy()
+
+
 def test_grid_4096():
     g = synth.grid_4096()
     G = abfs.graph_create(g.colptr, g.rowidx, directed=False)
