@@ -52,8 +52,10 @@ def _peaks():
 def _engine_sha256() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("engine.cu", "internal.h"):
-        with open(os.path.join(ROOT, "paper_1906_03113_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_1906_03113_gb300", "csrc")
+    names = sorted(f for f in os.listdir(csrc) if f.startswith("engine") and f.endswith((".cu", ".cuh")))
+    for f in names + ["internal.h"]:
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 

@@ -1,0 +1,248 @@
+// Engine building blocks: build options, memory-ordering helpers, the CTA's
+// shared state, scans and column lookups.
+// Part of the persistent engine (engine.cu), split by topic; included in order.
+#pragma once
+
+#include "internal.h"
+
+namespace abfs {
+
+// Longest sleep of an idle CTA between polls for work.
+#ifndef ABFS_IDLE_BACKOFF_NS
+#define ABFS_IDLE_BACKOFF_NS 2048
+#endif
+constexpr uint32_t kIdleBackoffMaxNs = ABFS_IDLE_BACKOFF_NS;
+
+// The phases and the expand loop are separate functions: each gets its own
+// register allocation, so the cold paths' state does not push the hot loop
+// into spills.  -DABFS_INLINE_ALL inlines them instead.
+#ifdef ABFS_INLINE_ALL
+#define ABFS_NOINLINE
+#else
+#define ABFS_NOINLINE __noinline__
+#endif
+
+// ---------------------------------------------------------------------------
+// memory-ordering helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Read of data written earlier in this launch by other CTAs (L2, not L1).
+__device__ __forceinline__ uint32_t ld_l2(const uint32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ uint2 ld_l2(const uint2* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ld_l2(const unsigned long long* p) { return __ldcg(p); }
+// Read of data that no CTA writes during the launch.
+__device__ __forceinline__ uint32_t ld_ro(const uint32_t* p) { return __ldg(p); }
+// Read of data that no CTA writes during the current phase (the frozen test
+// bitmap): a plain load that may hit L1.  Every unit starts after an acquire
+// fence, which orders it after the writes of earlier phases.
+__device__ __forceinline__ uint32_t ld_frozen(const uint32_t* p) { return *p; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// shared state of one CTA
+// ---------------------------------------------------------------------------
+
+struct Cmd {
+    uint32_t has;      // 1 = a unit was taken
+    uint32_t q;        // instance
+    uint32_t epoch;
+    uint32_t unit;
+    uint32_t kind;
+    uint32_t level;
+    uint32_t nitems;
+    uint32_t last;     // this CTA completed the last unit of the phase
+    uint32_t quit;
+    uint32_t start;    // serving: this CTA claimed a newly submitted search
+};
+
+struct Smem {
+    // staged frontier vertices of the unit being expanded: id, column begin
+    // minus slot offset (row index of slot s is b[t] + s), slot offset, and
+    // end of the vertex's entry slots
+    uint32_t v[kTileMax + 1];
+    uint32_t b[kTileMax + 1];
+    uint32_t off[kTileMax + 1];
+    uint32_t end[kTileMax];
+    // bit (s - lo) set when slot s starts a staged vertex
+    uint32_t sbits[kStartWords];
+    // newly reached vertices staged per warp before a global append
+    uint32_t wv[kWarps][kWarpBuf];
+    uint32_t wcnt[kWarps];
+    uint32_t wvoff[kWarps + 1];
+    uint32_t wwoff[kWarps + 1];
+    uint32_t gbase;
+    uint32_t gblk;
+    unsigned long long geb;
+    uint32_t warp_sums[kWarps + 1];
+    // walk state of the current unit
+    uint32_t cur_b, cur_i, abort_unit, sub_cnt, sub_nseg;
+    // first staged vertex of each warp's slots (the expand loop's vb), kNoVb: none
+    uint32_t wvb[kWarps];
+    unsigned long long sub_g0, sub_end;
+    uint32_t seg_idx[32], seg_pos[32];
+    unsigned long long seg_eb[32];
+    unsigned long long st_read, st_unmasked, st_claims, st_nnz;
+    // resident narrow run: list counters and the search's state between levels
+    uint32_t nq_cnt, nt_cnt, nr_f, nr_reached, nr_shrinks, nr_stop, nr_sw, nr_mcur, nr_mprev;
+    unsigned long long nq_slots;
+    Cmd cmd;
+    Inst I;
+    uint32_t cur_q;
+    uint32_t prof_on;
+    uint32_t idle_exit;
+    unsigned long long prof[kProfSlots];
+};
+
+// Profiling runs: thread 0 adds the cycles since t0 to slot `slot`.
+__device__ __forceinline__ long long prof_now(const Smem& sm) {
+    return sm.prof_on ? clock64() : 0ll;
+}
+__device__ __forceinline__ void prof_add(Smem& sm, int slot, long long t0) {
+    if (sm.prof_on && threadIdx.x == 0) sm.prof[slot] += (unsigned long long)(clock64() - t0);
+}
+
+size_t engine_smem_bytes() { return sizeof(Smem); }
+
+// ---------------------------------------------------------------------------
+// block-level building blocks
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= (uint32_t)d) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan of a[0..cnt) in place; a[cnt] = total.  cnt <= kThreads*ITEMS.
+template <int ITEMS>
+__device__ void block_exclusive_scan(uint32_t* a, uint32_t cnt, Smem& sm) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t x[ITEMS];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < ITEMS; ++q) {
+        uint32_t idx = tid * ITEMS + q;
+        x[q] = idx < cnt ? a[idx] : 0u;
+        sum += x[q];
+    }
+    uint32_t incl = warp_incl_scan(sum);
+    if (lane == 31) sm.warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < (uint32_t)kWarps ? sm.warp_sums[lane] : 0u;
+        uint32_t si = warp_incl_scan(s);
+        if (lane < (uint32_t)kWarps) sm.warp_sums[lane] = si - s;
+        if (lane == kWarps - 1) sm.warp_sums[kWarps] = si;
+    }
+    __syncthreads();
+    uint32_t run = sm.warp_sums[warp] + incl - sum;
+#pragma unroll
+    for (int q = 0; q < ITEMS; ++q) {
+        uint32_t idx = tid * ITEMS + q;
+        if (idx < cnt) a[idx] = run;
+        run += x[q];
+    }
+    if (tid == 0) a[cnt] = sm.warp_sums[kWarps];
+    __syncthreads();
+}
+constexpr int kTileItems = (kTileMax + kThreads - 1) / kThreads;
+
+// Column of vertex v in matrix `mat` (0 = input, 1/2 = shrunk copies).
+struct ColRef {
+    uint32_t beg;
+    uint32_t len;
+};
+
+__device__ __forceinline__ ColRef col_of(const Inst& I, uint32_t mat, uint32_t v) {
+    ColRef c;
+    if (mat == 0) {
+        const uint32_t b = ld_ro(I.colptr + v);
+        const uint32_t e = ld_ro(I.colptr + v + 1);
+        c.beg = b;
+        c.len = e - b;
+    } else {
+        c.beg = ld_l2(I.sbeg[mat - 1] + v);
+        c.len = ld_l2(I.slen[mat - 1] + v);
+    }
+    return c;
+}
+
+__device__ __forceinline__ const uint32_t* rows_of(const Inst& I, uint32_t mat) {
+    return mat == 0 ? I.rowidx : I.srows[mat - 1];
+}
+
+__device__ __forceinline__ uint32_t mat_for_level(const InstCtl* ctl, uint32_t lvl) {
+    // mat_cur/mat_prev/mat_switch change only between phases; the acquire at
+    // the start of a unit orders these reads.
+    const uint32_t sw = ld_relaxed(&ctl->mat_switch);
+    return lvl >= sw ? ld_relaxed(&ctl->mat_cur) : ld_relaxed(&ctl->mat_prev);
+}
+
+// Matrices read by levels k and k+1, from one round of independent loads.
+__device__ __forceinline__ void level_mats(const InstCtl* ctl, uint32_t k, uint32_t& mat,
+                                           uint32_t& mat_next) {
+    const uint32_t sw = ld_relaxed(&ctl->mat_switch);
+    const uint32_t cur = ld_relaxed(&ctl->mat_cur);
+    const uint32_t prev = ld_relaxed(&ctl->mat_prev);
+    mat = k >= sw ? cur : prev;
+    mat_next = k + 1 >= sw ? cur : prev;
+}
+
+__device__ __forceinline__ void fail(InstCtl* ctl, uint32_t code) { atomicCAS(&ctl->err, 0u, code); }
+
+// L2 policy for the streamed row indices: evict first, so the search's hot
+// state (bitmaps, parents, column pointers, queues) stays resident.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// Row index load: the input matrix never changes during a launch (read-only
+// path); shrunk copies are written by earlier phases of the same launch.
+__device__ __forceinline__ uint32_t ld_row(const uint32_t* rows, uint32_t idx, uint32_t mat,
+                                           uint64_t pol) {
+    uint32_t v;
+    if (mat == 0)
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;"
+            : "=r"(v)
+            : "l"(rows + idx), "l"(pol));
+    else
+        asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;"
+                     : "=r"(v)
+                     : "l"(rows + idx), "l"(pol)
+                     : "memory");
+    return v;
+}
+
+}  // namespace abfs
