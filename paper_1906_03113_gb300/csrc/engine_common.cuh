@@ -81,6 +81,19 @@ struct Cmd {
     uint32_t start;    // serving: this CTA claimed a newly submitted search
 };
 
+// The phase of the last unit this CTA took: a further unit of the same phase
+// needs neither the acquire fence nor the phase's fields again.
+struct RanPhase {
+    uint32_t valid;
+    uint32_t fresh;   // a unit of the phase just completed (not the last one)
+    uint32_t q;
+    uint32_t epoch;
+    uint32_t kind;
+    uint32_t level;
+    uint32_t nitems;
+    unsigned long long desc;  // [epoch:32][units:32] of the phase
+};
+
 struct Smem {
     // staged frontier vertices of the unit being expanded: id, column begin
     // minus slot offset (row index of slot s is b[t] + s), slot offset, and
@@ -112,6 +125,7 @@ struct Smem {
     uint32_t nq_cnt, nt_cnt, nr_f, nr_reached, nr_shrinks, nr_stop, nr_sw, nr_mcur, nr_mprev;
     unsigned long long nq_slots;
     Cmd cmd;
+    RanPhase ran;
     Inst I;
     uint32_t cur_q;
     uint32_t prof_on;

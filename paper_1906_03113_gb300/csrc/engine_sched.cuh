@@ -51,6 +51,7 @@ __device__ __forceinline__ bool take_unit(const EngineArgs& a, uint32_t q, Smem&
         __threadfence();  // acquire: the descriptor the host wrote before the state
         sm.cmd.q = q;
         sm.cmd.start = 1;
+        sm.ran.valid = 0;
         return true;
     }
     InstCtl* ctl = ctl_of(a, q);
@@ -60,15 +61,30 @@ __device__ __forceinline__ bool take_unit(const EngineArgs& a, uint32_t q, Smem&
     const unsigned long long d =
         (e == e_seen && (uint32_t)(d_seen >> 32) == e) ? d_seen : ld_relaxed64(&ctl->desc[e & 1]);
     if ((uint32_t)(d >> 32) != e || t >= (uint32_t)d) return false;
-    __threadfence();  // acquire: the phase fields and the data of earlier phases
-    const uint32_t qq = e & 1;
     sm.cmd.q = q;
     sm.cmd.start = 0;
     sm.cmd.epoch = e;
     sm.cmd.unit = t;
+    if (sm.ran.valid && sm.ran.q == q && sm.ran.epoch == e) {
+        // a further unit of the phase this CTA took a unit of before: that
+        // take's acquire and the phase's fields still hold
+        sm.cmd.kind = sm.ran.kind;
+        sm.cmd.level = sm.ran.level;
+        sm.cmd.nitems = sm.ran.nitems;
+        return true;
+    }
+    __threadfence();  // acquire: the phase fields and the data of earlier phases
+    const uint32_t qq = e & 1;
     sm.cmd.kind = ld_relaxed(&ctl->kind[qq]);
     sm.cmd.level = ld_relaxed(&ctl->plevel[qq]);
     sm.cmd.nitems = ld_relaxed(&ctl->nitems[qq]);
+    sm.ran.valid = 1;
+    sm.ran.q = q;
+    sm.ran.epoch = e;
+    sm.ran.kind = sm.cmd.kind;
+    sm.ran.level = sm.cmd.level;
+    sm.ran.nitems = sm.cmd.nitems;
+    sm.ran.desc = d;
     return true;
 }
 
@@ -117,6 +133,16 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
     if (threadIdx.x < 32) {
         const uint32_t lane = threadIdx.x;
         bool got = false;
+        if (sm.ran.valid && sm.ran.fresh) {
+            // right after a unit that did not end its phase, first try that
+            // phase again without polling (an idle CTA polls instead)
+            bool ok = false;
+            if (lane == 0) {
+                ok = take_unit(a, sm.ran.q, sm, sm.ran.epoch, sm.ran.desc);
+                sm.ran.fresh = 0;
+            }
+            got = __shfl_sync(0xFFFFFFFFu, ok, 0);
+        }
         for (uint32_t base = 0; base < a.ninst && !got; base += 32) {
             const uint32_t idx = base + lane;
             const uint32_t q = (cursor + idx) % a.ninst;
@@ -162,6 +188,7 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
     if (threadIdx.x == 0) {
         const uint32_t left = atomicSub(&ctl->pending[epoch & 1], 1u);
         sm.cmd.last = (left == 1);
+        sm.ran.fresh = left != 1;
         atomicAdd(a.heartbeat, 1ull);
     }
     __syncthreads();
@@ -185,6 +212,8 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) engine_kernel(EngineArgs a
         for (int q = 0; q < kProfSlots; ++q) sm.prof[q] = 0;
         sm.st_read = sm.st_unmasked = sm.st_claims = sm.st_nnz = 0;
         sm.cur_q = kUnset;
+        sm.ran.valid = 0;
+        sm.ran.fresh = 0;
     }
     __syncthreads();
     uint32_t cursor = blockIdx.x % a.ninst;
