@@ -461,6 +461,9 @@ template <int MODE>
 __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                         uint32_t kind, uint32_t k, uint32_t* done_count,
                         unsigned long long* heartbeat) {
+    // the search's phase counter: written only by the advancing CTA, visible
+    // here since this CTA took a unit of the current phase
+    const uint32_t epoch0 = threadIdx.x == 0 ? ld_relaxed(&ctl->epoch) : 0u;
     for (;;) {
         if (threadIdx.x == 0) {
             __threadfence();
@@ -513,18 +516,28 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
             trace_put(I, ctl, nkind, nk, alone, nkind == kPhPlainMask ? ni : units, nf, ne);
         if (!alone) {
             if (threadIdx.x == 0) {
-                const uint32_t e = ld_relaxed(&ctl->epoch) + 1;
+                const uint32_t e = epoch0 + 1;
                 const uint32_t q = e & 1;
+                const unsigned long long d = ((unsigned long long)e << 32) | units;
                 st_relaxed(&ctl->kind[q], nkind);
                 st_relaxed(&ctl->plevel[q], nk);
                 st_relaxed(&ctl->nitems[q], ni);
                 st_relaxed(&ctl->pending[q], units);
                 st_relaxed(&ctl->epoch, e);
-                st_relaxed(&ctl->wide_levels, ld_relaxed(&ctl->wide_levels) + 1);
-                __threadfence();
-                atomicExch(&ctl->desc[q], ((unsigned long long)e << 32) | units);
-                __threadfence();
-                atomicExch(&ctl->grab, (unsigned long long)e << 32);
+                atomicAdd(&ctl->wide_levels, 1u);
+                st_relaxed64(&ctl->desc[q], d);
+                // the phase becomes takeable only after all of the above
+                st_release64(&ctl->grab, (unsigned long long)e << 32);
+                // this CTA knows the phase it published: its first take needs
+                // neither a poll nor a second acquire
+                sm.ran.valid = 1;
+                sm.ran.fresh = 1;
+                sm.ran.q = sm.cmd.q;
+                sm.ran.epoch = e;
+                sm.ran.kind = nkind;
+                sm.ran.level = nk;
+                sm.ran.nitems = ni;
+                sm.ran.desc = d;
             }
             __syncthreads();
             return;
