@@ -59,7 +59,7 @@ typedef enum {
     ABFS_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out; the kernel returned */
     ABFS_ERR_BUSY = 6,          /* serving: the request was not admitted (no slot / memory) */
     ABFS_ERR_DEVICE = 7,        /* a device-side consistency check failed (capacity, bounds) */
-    ABFS_ERR_UNSUPPORTED = 8,   /* size beyond this build's limits, or a feature the mode lacks */
+    ABFS_ERR_UNSUPPORTED = 8,   /* size beyond the library's limits, or a feature the mode lacks */
     ABFS_ERR_NOT_FOUND = 9      /* serving: unknown ticket */
 } abfs_status;
 

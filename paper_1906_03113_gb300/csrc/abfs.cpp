@@ -35,7 +35,7 @@ extern "C" const char* abfs_strerror(int status) {
         case ABFS_ERR_TIMEOUT: return "bounded device wait expired";
         case ABFS_ERR_BUSY: return "not admitted: no free slot or memory";
         case ABFS_ERR_DEVICE: return "device-side consistency check failed";
-        case ABFS_ERR_UNSUPPORTED: return "size beyond this build's limits";
+        case ABFS_ERR_UNSUPPORTED: return "size beyond the library's limits, or unsupported in this mode";
         case ABFS_ERR_NOT_FOUND: return "unknown ticket";
         default: return "unknown status";
     }
