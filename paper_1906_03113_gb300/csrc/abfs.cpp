@@ -287,6 +287,7 @@ struct abfs_graph_s {
     uint64_t nnz = 0;
     int directed = 0;
     bool sorted = false;          // every column's row indices ascend (bottom-up levels allowed)
+    uint32_t* d_inb = nullptr;    // rows that occur in some column, one bit per vertex
     int device = 0;
     int sms = 0;
     bool tuned = false;
@@ -336,6 +337,7 @@ Inst make_inst(const abfs_graph_s* g, char* base, const Layout& L, uint32_t src,
     Inst I = make_inst_raw(g->d_colptr, g->d_rowidx, g->n, base, L, src, level, parent);
     // the hybrid's bottom-up levels need a symmetric pattern and ascending columns
     I.bu_ok = (!g->directed && g->sorted) ? 1u : 0u;
+    I.inb = g->d_inb;
     return I;
 }
 
@@ -511,6 +513,12 @@ extern "C" int abfs_graph_create(const uint32_t* colptr, const uint32_t* rowidx,
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dev_free(d_flag);
     g->sorted = unsorted == 0;
+    // the rows that occur at all: the others are never reached
+    const uint32_t nwords = (n + 31) / 32;
+    if (e == cudaSuccess && dev_alloc((void**)&g->d_inb, (size_t)nwords * 4) != ABFS_OK)
+        e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = launch_row_bitmap(g->d_rowidx, nnz, g->d_inb, nwords, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->last_use, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         abfs_graph_destroy(g);
@@ -528,6 +536,7 @@ extern "C" int abfs_graph_destroy(abfs_graph_t g) {
     dev_free(g->d_parent);
     dev_free(g->d_colptr);
     dev_free(g->d_rowidx);
+    dev_free(g->d_inb);
     if (g->last_use) cudaEventDestroy(g->last_use);
     delete g;
     return ABFS_OK;

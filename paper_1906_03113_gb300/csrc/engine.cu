@@ -74,9 +74,17 @@ __global__ void init_fill_kernel(const Inst* insts, uint32_t ninst, uint32_t mod
         if (I.sigma) I.sigma[v] = 0ull;
     }
     if (mode == kModeSub) {
+        // vertices that no column contains cannot be reached: they start out in
+        // both visited bitmaps, so no later pass (extraction, bottom-up levels)
+        // looks at them again
         for (uint32_t w = t0; w < I.nwords; w += stride) {
-            I.bm[0][w] = 0u;
-            I.bm[1][w] = 0u;
+            uint32_t m = 0u;
+            if (I.inb) {
+                m = ~I.inb[w];
+                if (w == I.nwords - 1 && (I.n & 31)) m &= (1u << (I.n & 31)) - 1u;
+            }
+            I.bm[0][w] = m;
+            I.bm[1][w] = m;
         }
     }
     if (blockIdx.x == 0) {
@@ -179,6 +187,28 @@ cudaError_t launch_sorted_check(const uint32_t* colptr, const uint32_t* rowidx, 
     if (blocks > 2048) blocks = 2048;
     if (blocks == 0) blocks = 1;
     sorted_check_kernel<<<blocks, 256, 0, s>>>(colptr, rowidx, n, unsorted);
+    return cudaGetLastError();
+}
+
+// Sets bit r of `bits` for every row index r stored in the matrix (bits must be
+// zero on entry).  Once per graph.
+__global__ void row_bitmap_kernel(const uint32_t* rowidx, uint64_t nnz, uint32_t* bits) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        const uint32_t r = rowidx[e];
+        const uint32_t bit = 1u << (r & 31);
+        // most rows repeat: skip the atomic when the bit is already visible
+        if (!(__ldcg(bits + (r >> 5)) & bit)) atomicOr(bits + (r >> 5), bit);
+    }
+}
+
+cudaError_t launch_row_bitmap(const uint32_t* rowidx, uint64_t nnz, uint32_t* bits, uint32_t nwords,
+                              cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(bits, 0, (size_t)nwords * 4, s);
+    if (e != cudaSuccess || nnz == 0) return e;
+    uint64_t blocks = (nnz + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    row_bitmap_kernel<<<(unsigned)blocks, 256, 0, s>>>(rowidx, nnz, bits);
     return cudaGetLastError();
 }
 

@@ -139,6 +139,8 @@ struct Inst {
     unsigned long long* sigma;  // optional output: shortest-path counts mod 2^64 (nullptr = off)
     uint32_t* bm[2];         // visited bitmaps, ping-pong by level parity
     uint32_t* fbm[2];        // hybrid: frontier bitmaps of bottom-up levels, by level parity
+    const uint32_t* inb;     // rows that occur in some column (nullptr: not known); the
+                             // others can never be reached and start out masked
     uint32_t bu_ok;          // hybrid: bottom-up levels allowed (undirected, sorted columns, no counts)
     uint32_t* fq[2];         // frontier vertices, by level parity
     uint32_t* fbeg[2];       // their column begins (kUnset: no entries)
@@ -241,6 +243,8 @@ int graph_arrays(abfs_graph_t g, const uint32_t** colptr, const uint32_t** rowid
 cudaError_t launch_put_inst(const Inst& inst, Inst* dst, cudaStream_t s);
 cudaError_t launch_sorted_check(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n,
                                 uint32_t* unsorted, cudaStream_t s);
+cudaError_t launch_row_bitmap(const uint32_t* rowidx, uint64_t nnz, uint32_t* bits, uint32_t nwords,
+                              cudaStream_t s);
 cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
                              unsigned long long* sigma, uint32_t bu_ok,
                              uint4* trace, uint32_t trace_cap, cudaStream_t s);
