@@ -240,6 +240,16 @@ int abfs_run_batch(const abfs_graph_t* g, const uint32_t* sources, uint32_t coun
 int abfs_batch_create(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
                       int32_t* const* level, int32_t* const* parent, const abfs_params* params,
                       abfs_stream_t stream, abfs_batch_t* out);
+/*
+ * The same plan with shortest-path counts (as abfs_run_counts): sigma[i] is a
+ * caller-owned DEVICE buffer of g[i]'s n uint64, written modulo 2^64 on every
+ * replay.  Submatrix mode only (ABFS_ERR_UNSUPPORTED otherwise); a NULL sigma
+ * array or entry is ABFS_ERR_INVALID_ARG.  Searches with counts stay top-down.
+ */
+int abfs_batch_create_counts(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
+                             int32_t* const* level, int32_t* const* parent,
+                             uint64_t* const* sigma, const abfs_params* params,
+                             abfs_stream_t stream, abfs_batch_t* out);
 int abfs_batch_launch(abfs_batch_t b, abfs_stream_t stream);
 /* Copies per-instance statuses (host array of count) after a launch; synchronises. */
 int abfs_batch_status(abfs_batch_t b, abfs_stream_t stream, int32_t* status_per_query);

@@ -155,6 +155,8 @@ def load():
         "abfs_run_trace": ([vp, u32, vp, vp, vp, P(Params), vp, u32, P(u32)], c_int),
         "abfs_run_batch": ([P(vp), P(u32), u32, P(vp), P(vp), vp, P(Params), P(i32)], c_int),
         "abfs_batch_create": ([P(vp), P(u32), u32, P(vp), P(vp), P(Params), vp, P(vp)], c_int),
+        "abfs_batch_create_counts": ([P(vp), P(u32), u32, P(vp), P(vp), P(vp), P(Params), vp, P(vp)],
+                                     c_int),
         "abfs_batch_launch": ([vp, vp], c_int),
         "abfs_batch_status": ([vp, vp, P(i32)], c_int),
         "abfs_batch_destroy": ([vp], c_int),
@@ -414,21 +416,31 @@ class BatchPlan:
     initialisation + persistent launch captured in a CUDA graph."""
 
     def __init__(self, graphs: list[Graph], sources, levels=None, parents=None,
-                 params: Params | None = None, stream=None):
+                 params: Params | None = None, stream=None, counts: bool = False):
+        """counts=True: abfs_batch_create_counts, with int64 tensors (uint64 path
+        counts mod 2^64) in self.sigmas."""
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         self.graphs = list(graphs)
         self.count = len(graphs)
         self.levels = levels or [torch.empty(g.n, dtype=torch.int32, device=dev) for g in graphs]
         self.parents = parents or [torch.empty(g.n, dtype=torch.int32, device=dev) for g in graphs]
+        self.sigmas = [torch.empty(g.n, dtype=torch.int64, device=dev) for g in graphs] if counts else None
         src = (ctypes.c_uint32 * self.count)(*[int(s) for s in sources])
         h = ctypes.c_void_p()
-        rc = load().abfs_batch_create(_ptr_array([g.handle.value for g in graphs]), src, self.count,
-                                      _ptr_array([t.data_ptr() for t in self.levels]),
-                                      _ptr_array([t.data_ptr() for t in self.parents]),
-                                      ctypes.byref(params) if params else None,
-                                      _stream_ptr(stream), ctypes.byref(h))
-        _check(rc, "abfs_batch_create")
+        gp = _ptr_array([g.handle.value for g in graphs])
+        lp = _ptr_array([t.data_ptr() for t in self.levels])
+        pp = _ptr_array([t.data_ptr() for t in self.parents])
+        pr = ctypes.byref(params) if params else None
+        if counts:
+            rc = load().abfs_batch_create_counts(gp, src, self.count, lp, pp,
+                                                 _ptr_array([t.data_ptr() for t in self.sigmas]),
+                                                 pr, _stream_ptr(stream), ctypes.byref(h))
+            _check(rc, "abfs_batch_create_counts")
+        else:
+            rc = load().abfs_batch_create(gp, src, self.count, lp, pp, pr, _stream_ptr(stream),
+                                          ctypes.byref(h))
+            _check(rc, "abfs_batch_create")
         self.handle = h
 
     def launch(self, stream=None) -> None:

@@ -704,18 +704,21 @@ extern "C" int abfs_batch_destroy(abfs_batch_t b) {
     return ABFS_OK;
 }
 
-extern "C" int abfs_batch_create(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
-                                 int32_t* const* level, int32_t* const* parent,
-                                 const abfs_params* params, abfs_stream_t stream,
-                                 abfs_batch_t* out) {
+namespace {
+// Shared by abfs_batch_create and abfs_batch_create_counts (sigma == NULL: no counts).
+int batch_create(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
+                 int32_t* const* level, int32_t* const* parent, uint64_t* const* sigma,
+                 const abfs_params* params, abfs_batch_t* out) {
     if (!g || !sources || !level || !parent || !out || count == 0) return ABFS_ERR_INVALID_ARG;
     *out = nullptr;
     abfs_params tmp;
     const abfs_params& p = pick_params(g[0], params, tmp);
     int rc = check_params(p);
     if (rc) return rc;
+    if (sigma && p.mode != ABFS_MODE_SUBMATRIX) return ABFS_ERR_UNSUPPORTED;
     for (uint32_t i = 0; i < count; ++i) {
         if (!g[i] || !level[i] || !parent[i] || sources[i] >= g[i]->n) return ABFS_ERR_INVALID_ARG;
+        if (sigma && !sigma[i]) return ABFS_ERR_INVALID_ARG;
         if (g[i]->device != g[0]->device) return ABFS_ERR_INVALID_ARG;
     }
     abfs_batch_s* b = new (std::nothrow) abfs_batch_s();
@@ -750,6 +753,11 @@ extern "C" int abfs_batch_create(const abfs_graph_t* g, const uint32_t* sources,
     b->ctl_off.resize(count);
     for (uint32_t i = 0; i < count; ++i) {
         hI[i] = make_inst(g[i], b->ws + base[i], L[i], sources[i], level[i], parent[i]);
+        if (sigma) {
+            // path counts: every multiplied entry contributes, so the search stays top-down
+            hI[i].sigma = reinterpret_cast<unsigned long long*>(sigma[i]);
+            hI[i].bu_ok = 0;
+        }
         b->ctl_off[i] = base[i] + L[i].ctl;
     }
     cudaError_t e = cudaMemcpy(b->d_insts, hI.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice);
@@ -788,9 +796,27 @@ extern "C" int abfs_batch_create(const abfs_graph_t* g, const uint32_t* sources,
         abfs_batch_destroy(b);
         return cuda_fail(e);
     }
-    (void)stream;
     *out = b;
     return ABFS_OK;
+}
+}  // namespace
+
+extern "C" int abfs_batch_create(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
+                                 int32_t* const* level, int32_t* const* parent,
+                                 const abfs_params* params, abfs_stream_t stream,
+                                 abfs_batch_t* out) {
+    (void)stream;
+    return batch_create(g, sources, count, level, parent, nullptr, params, out);
+}
+
+extern "C" int abfs_batch_create_counts(const abfs_graph_t* g, const uint32_t* sources,
+                                        uint32_t count, int32_t* const* level,
+                                        int32_t* const* parent, uint64_t* const* sigma,
+                                        const abfs_params* params, abfs_stream_t stream,
+                                        abfs_batch_t* out) {
+    (void)stream;
+    if (!sigma) return ABFS_ERR_INVALID_ARG;
+    return batch_create(g, sources, count, level, parent, sigma, params, out);
 }
 
 extern "C" int abfs_batch_launch(abfs_batch_t b, abfs_stream_t stream) {

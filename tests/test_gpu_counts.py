@@ -112,6 +112,33 @@ def test_hypercube_factorials(d):
     G.destroy()
 
 
+def test_batch_plan_with_counts(small):
+    """A mixed batch with path counts in one launch (replayed twice, hybrid
+    parameters given: searches with counts stay top-down) equals the oracle."""
+    gs, dev = small
+    names = ["er_2_16", "rmat_14", "grid_100x37", "rgg_2_15", "star", "path_3000", "no_edges",
+             "dicycle_777", "one_vertex"]
+    graphs, srcs, hosts = [], [], []
+    for nm in names:
+        for s in _sources(gs[nm])[:2]:
+            graphs.append(dev[nm])
+            srcs.append(s)
+            hosts.append(gs[nm])
+    for p in (_params(), _params(bottom_up_alpha=5, bottom_up_beta=24)):
+        plan = abfs.BatchPlan(graphs, srcs, params=p, counts=True)
+        for rep in range(2):
+            for t in plan.sigmas:
+                t.fill_(7)
+            plan.launch()
+            assert plan.status() == [0] * len(graphs)
+            for g, s, L, P, S in zip(hosts, srcs, plan.levels, plan.parents, plan.sigmas):
+                _check_counts(g, s, L, P, S, f"batch counts {g.name} src{s} rep{rep}")
+        plan.destroy()
+    with pytest.raises(abfs.AbfsError) as ei:
+        abfs.BatchPlan(graphs[:1], srcs[:1], params=_params(mode=PLAIN), counts=True)
+    assert ei.value.status == 8  # ABFS_ERR_UNSUPPORTED
+
+
 # ---------------------------------------------------------------------------
 # full-size workloads
 # ---------------------------------------------------------------------------
