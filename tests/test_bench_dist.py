@@ -65,3 +65,25 @@ def test_reference_arm_runs_on_rank_zero_only():
     with contextlib.redirect_stdout(buf):
         bench.run_reference(Args(), 2, 1)
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_line_on_rank_zero():
+    """The reference arm's JSON line carries the contract's keys and times the
+    oracle on the host (ER 2^16, one step)."""
+    import json
+
+    class Args:
+        workload = "er16"
+        steps = 2
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(Args(), 1, 0)
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["metric"] == "GTEPS" and line["value"] > 0
+    assert line["config"]["workload"] == "er16_src0"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
