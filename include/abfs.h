@@ -193,7 +193,9 @@ int abfs_run_counts(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* pa
 /*
  * Same search, end to end through host memory: copies the source in, runs,
  * and copies level/parent back into HOST buffers of n int32 each (pinned
- * memory gives full copy bandwidth).  Synchronises `stream`.
+ * memory gives full copy bandwidth).  Synchronises `stream` and returns the
+ * search's own status (ABFS_ERR_TIMEOUT or ABFS_ERR_DEVICE if the device side
+ * failed).
  */
 int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_host, int32_t* parent_host,
                   abfs_stream_t stream, const abfs_params* params, abfs_stats* stats);
@@ -374,6 +376,19 @@ int abfs_run_static(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, 
  */
 int abfs_set_allocator(void* (*alloc)(size_t bytes, void* ctx), void (*free_fn)(void* ptr, void* ctx),
                        void* ctx);
+
+/*
+ * Test control for the bounded device waits; the paper has no counterpart.
+ * While extra_units is non-zero, every search started afterwards (abfs_run,
+ * abfs_run_counts, abfs_run_host, abfs_run_trace, abfs_run_batch, and batch
+ * plans created afterwards) publishes its first phase as waiting for
+ * extra_units more work units than it has.  That phase never completes, the
+ * engine's CTAs find no work, their idle wait -- bounded by
+ * abfs_params.timeout_ms without progress -- runs out, and the search ends
+ * with ABFS_ERR_TIMEOUT while the launch returns normally: no fault, no hang.
+ * 0 restores normal operation.  Process-wide; needs no device.
+ */
+int abfs_test_hold_first_phase(uint32_t extra_units);
 
 /* On-chip ceilings of the expand step, measured on the current device. */
 typedef struct {

@@ -165,6 +165,7 @@ def load():
         "abfs_batch_tune": ([P(vp), P(u32), u32, u32, ctypes.c_char_p, vp, P(Params),
                              P(ctypes.c_float)], c_int),
         "abfs_set_allocator": ([vp, vp, vp], c_int),
+        "abfs_test_hold_first_phase": ([u32], c_int),
         "abfs_check_params": ([P(Params)], c_int),
         "abfs_run_static": ([vp, vp, u32, u64, u32, vp, vp, vp], c_int),
         "abfs_serve_default_cfg": ([P(ServeCfg)], c_int),

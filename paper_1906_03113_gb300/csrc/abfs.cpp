@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -425,6 +426,7 @@ int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* pa
     a.stop_flag = nullptr;
     a.idle_exit_ns = 0;
     a.p = engine_params(p);
+    a.hold_units = test_hold_units();
     CK(launch_init(a, g->n, s));
     CK(launch_engine(a, grid_size(g, p, 0), s));
     CK(cudaEventRecord(g->last_use, s));
@@ -611,9 +613,9 @@ extern "C" int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_hos
     if (rc) return rc;
     CK(cudaMemcpyAsync(level_host, g->d_level, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(parent_host, g->d_parent, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
-    if (stats) return finish_stats(g, s, stats);
-    CK(cudaStreamSynchronize(s));
-    return ABFS_OK;
+    // the call synchronises anyway: it returns the search's own status
+    abfs_stats local;
+    return finish_stats(g, s, stats ? stats : &local);
 }
 
 extern "C" int abfs_run_trace(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,
@@ -783,6 +785,7 @@ int batch_create(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
     a.stop_flag = nullptr;
     a.idle_exit_ns = 0;
     a.p = engine_params(p);
+    a.hold_units = test_hold_units();
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t e1 = launch_init(a, max_n, cap);
@@ -1049,6 +1052,23 @@ extern "C" int abfs_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)
 }
 
 extern "C" const char* abfs_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// test control: a first phase that never completes
+// ---------------------------------------------------------------------------
+
+namespace {
+std::atomic<uint32_t> g_hold_units{0};
+}  // namespace
+
+namespace abfs {
+uint32_t test_hold_units() { return g_hold_units.load(std::memory_order_relaxed); }
+}  // namespace abfs
+
+extern "C" int abfs_test_hold_first_phase(uint32_t extra_units) {
+    g_hold_units.store(extra_units, std::memory_order_relaxed);
+    return ABFS_OK;
+}
 
 // ---------------------------------------------------------------------------
 // batch autotuner

@@ -129,7 +129,7 @@ __global__ void init_source_kernel(EngineArgs a) {
     ctl->kind[0] = kPhStart;
     ctl->plevel[0] = 0;
     ctl->nitems[0] = 0;
-    ctl->pending[0] = 1;
+    ctl->pending[0] = 1 + a.hold_units;
     ctl->epoch = 0;
     ctl->desc[0] = (0ull << 32) | 1ull;
     ctl->desc[1] = ~0ull;

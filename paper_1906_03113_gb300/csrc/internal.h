@@ -190,6 +190,10 @@ struct EngineArgs {
     const uint32_t* stop_flag;     // serving: host sets 1 to end the launch
     unsigned long long idle_exit_ns;  // serving: the launch ends after this long without progress
     EngineParams p;
+    // test control (abfs_test_hold_first_phase): units the first phase of every
+    // search waits for beyond its own, so it never completes and the bounded
+    // idle wait runs out; 0 in normal operation
+    uint32_t hold_units = 0;
 };
 
 // Cycle accounting of the engine's CTAs (profiling runs only).
@@ -238,6 +242,9 @@ Inst make_inst_raw(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, c
 int grid_for(int sms, const abfs_params& p);
 int graph_arrays(abfs_graph_t g, const uint32_t** colptr, const uint32_t** rowidx, uint32_t* n,
                  uint64_t* nnz, int* device, int* sms);
+
+// Test control set by abfs_test_hold_first_phase (abfs.cpp).
+uint32_t test_hold_units();
 
 // Launch helpers implemented in engine.cu.
 cudaError_t launch_put_inst(const Inst& inst, Inst* dst, cudaStream_t s);

@@ -201,6 +201,7 @@ def test_repeated_runs_identical(small):
     for _ in range(5):
         level, parent = abfs.run(dev["rmat_14"], s)
         cur = (level.cpu().numpy().copy(), parent.cpu().numpy().copy())
+        _check(g, s, cur[0], cur[1], "repeated run")
         if ref is not None:
             assert np.array_equal(ref[0], cur[0]) and np.array_equal(ref[1], cur[1])
         ref = cur
@@ -401,14 +402,14 @@ def test_rmat22_batch_64_sources(rmat22):
     levels, parents, st = abfs.run_batch([G] * 64, srcs)
     torch.cuda.synchronize()
     assert all(x == 0 for x in st)
-    for i in (0, 17, 63):
+    for i in range(64):
         _check(g, int(srcs[i]), levels[i], parents[i], f"rmat22 batch {i}")
 
 
 def test_batch_512_graphs_as_benchmarked():
     """The benchmark's 512-graph batch (seeded ER/R-MAT, n in [2^10, 2^18]) in one
     persistent launch with the batch autotuner's parameters: every status is OK
-    and a seeded sample of 48 searches equals the oracle bit for bit."""
+    and every one of the 512 searches equals the oracle bit for bit."""
     specs = synth.batch_specs(512, seed=1)
     hosts = [synth.make_batch_graph(sp) for sp in specs]
     graphs = [abfs.graph_create(h.colptr, h.rowidx, directed=False) for h in hosts]
@@ -418,8 +419,7 @@ def test_batch_512_graphs_as_benchmarked():
         plan = abfs.BatchPlan(graphs, srcs, params=p)
         plan.launch()
         assert plan.status() == [0] * len(graphs)
-        rng = np.random.default_rng(11)
-        for i in rng.choice(len(graphs), size=48, replace=False).tolist():
+        for i in range(len(graphs)):
             _check(hosts[i], srcs[i], plan.levels[i], plan.parents[i], f"batch512 graph {i}")
         plan.destroy()
     for G in graphs:

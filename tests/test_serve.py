@@ -1,11 +1,15 @@
-"""Serving (continuous batching): every result equals the same query run alone.
+"""Serving (continuous batching): every result equals the oracle's and the
+same query run alone.
 
 Queries arrive in bursts while others are on the device; a small memory
-budget forces memory-gated admission.  The bar is bit-exact equality with
-abfs_run (itself equal to the oracle)."""
+budget forces memory-gated admission.  The bar is bit-exact equality of every
+served level[] and parent[] with the CPU oracle (the result definition of
+Theorem 1: hop distance and least-index parent), and with abfs_run of the same
+query on the same GPU."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -74,7 +78,16 @@ def _serve_and_check(gs, dev, queries, cfg, bursts):
     assert rep["completed"] == len(queries) == rep["submitted"] and rep["failed"] == 0
     assert rep["launches"] >= 1 and 0 < rep["p50_ms"] <= rep["p99_ms"] <= rep["max_ms"]
     torch.cuda.synchronize()
+    expect = {}
     for gi, s, lev, par in outs:
+        if (gi, s) not in expect:
+            expect[(gi, s)] = oracle.bfs(gs[gi], s)
+        lo, po = expect[(gi, s)]
+        lev_h, par_h = lev.cpu().numpy(), par.cpu().numpy()
+        bad = np.nonzero(lev_h != lo)[0]
+        assert bad.size == 0, f"served level != oracle: graph {gi} src {s} at {bad[:8]}"
+        bad = np.nonzero(par_h != po)[0]
+        assert bad.size == 0, f"served parent != oracle: graph {gi} src {s} at {bad[:8]}"
         la, pa = abfs.run(dev[gi], s)
         assert torch.equal(la, lev) and torch.equal(pa, par), (gi, s)
     return rep
@@ -110,13 +123,18 @@ def test_serve_queue_full_is_busy(graphs):
             assert srv.wait(t, 60000) == 0
     rep = srv.stop()
     assert rep["completed"] == sum(r is not None for r in results)
+    torch.cuda.synchronize()
+    lo, po = oracle.bfs(gs[0], 0)
+    for t, (lv, pr) in zip(results, bufs):
+        if t is not None:
+            assert np.array_equal(lv.cpu().numpy(), lo) and np.array_equal(pr.cpu().numpy(), po)
 
 
 @pytest.mark.gpu
 def test_serve_slot_reuse_under_churn():
     """Many short searches through few slots: each slot is reused hundreds of
     times while other CTAs still look at it, and every result still equals the
-    query run alone."""
+    oracle's and the query run alone."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     abfs.build()
