@@ -225,7 +225,10 @@ def run_reference(args, ws, rank):
 # ---------------------------------------------------------------------------
 
 def cpu_baseline(g, srcs, max_seconds=20.0):
-    """The oracle (sorted-frontier queue BFS, one thread) on a bounded sample."""
+    """The oracle (sorted-frontier queue BFS, one thread) on a bounded sample,
+    and beside it the paper's own CPU methods: sequential Algorithm 2 and
+    OpenMP Algorithm 3 on every host core (cpu_baselines/)."""
+    import cpu_baselines
     import oracle
     deg = g.degrees()
     edges, total, used = 0, 0.0, 0
@@ -238,24 +241,33 @@ def cpu_baseline(g, srcs, max_seconds=20.0):
         edges += nnz_c if g.directed else nnz_c // 2
         if total > max_seconds:
             break
-    return {"value": edges / total / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"{used} of the {len(srcs)} sources, one BFS each, on one host core "
-                      f"({total:.1f} s)"}
+    out = {"value": edges / total / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+           "sample": f"{used} of the {len(srcs)} sources, one BFS each, on one host core "
+                     f"({total:.1f} s)",
+           "host_cores": cpu_baselines.host_cores()}
+    try:
+        out["baselines"] = cpu_baselines.time_baselines(g, srcs, budget_s=max_seconds / 2, reps=5)
+    except Exception as exc:  # a baseline that cannot run is reported, not fatal
+        out["baselines"] = [{"error": f"{type(exc).__name__}: {exc}"}]
+    return out
 
 
 def _edges(st, directed):
     return st["nnz_reached"] if directed else st["nnz_reached"] / 2.0
 
 
-def bench_batch(args, ws, rank, local, torch, abfs, dist):
+def measure_batch(args, local, torch, abfs, big=None, G22=None, clocks=True):
     """512 ER/R-MAT graphs (n log-uniform in [2^10, 2^18], average degree U[4, 32])
     plus 64 sources on R-MAT-22, all in one persistent launch replayed from a
-    CUDA graph, against the same queries as single-query launches."""
+    CUDA graph, against the same queries as single-query launches.  Returns the
+    measurements as a dict (big, G22: an R-MAT-22 graph already built)."""
     specs = synth.batch_specs(512, seed=1)
     hosts = [synth.make_batch_graph(sp) for sp in specs]
-    big = synth.rmat_22()
+    own22 = big is None
+    if own22:
+        big = synth.rmat_22()
+        G22 = abfs.graph_create(big.colptr, big.rowidx, directed=False)
     graphs = [abfs.graph_create(h.colptr, h.rowidx, directed=False) for h in hosts]
-    G22 = abfs.graph_create(big.colptr, big.rowidx, directed=False)
     srcs = [int(synth.sources_with_degree(h, 1, seed=1 + i)[0]) if (h.degrees() > 0).any() else 0
             for i, h in enumerate(hosts)]
     src22 = [int(x) for x in synth.sources_with_degree(big, 64, seed=2)]
@@ -304,7 +316,7 @@ def bench_batch(args, ws, rank, local, torch, abfs, dist):
         torch.cuda.synchronize()
         return bms, a.elapsed_time(b), clk
 
-    batch_ms, single_ms, clk = batched_vs_single(qg, qs, Clocks(local))
+    batch_ms, single_ms, clk = batched_vs_single(qg, qs, Clocks(local) if clocks else None)
     parts = {}
     for name, lo, hi in (("512_graphs", 0, len(graphs)), ("rmat22_64_sources", len(graphs), len(qg))):
         bms, sms, _ = batched_vs_single(qg[lo:hi], qs[lo:hi])
@@ -321,34 +333,50 @@ def bench_batch(args, ws, rank, local, torch, abfs, dist):
               "batched_ms": hbms, "batched_gteps": total_edges / (hbms * 1e-3) / 1e9,
               "single_query_ms": hsms, "speedup_vs_single": hsms / hbms}
     nq = len(qg)
-    value, _ = job_throughput(total_edges, batch_ms, dist, "cuda")
+    for G in graphs:
+        G.destroy()
+    if own22:
+        G22.destroy()
+    return {"queries": nq, "steps": steps, "warmup": max(args.warmup, 3), "ms": batch_ms,
+            "total_edges": total_edges,
+            "queries_per_s": nq / (batch_ms * 1e-3),
+            "gteps": total_edges / (batch_ms * 1e-3) / 1e9,
+            "single_query_ms": single_ms,
+            "single_query_gteps": total_edges / (single_ms * 1e-3) / 1e9,
+            "speedup_vs_single": single_ms / batch_ms, "parts": parts,
+            "tuned_params": tuned.as_dict(), "tuner_ms": tuned_ms,
+            "launch": "one persistent launch (CUDA graph replay) of all 576 queries, parameters "
+                      "from the batch autotuner",
+            "graph": "512 ER/R-MAT graphs, n log-uniform in [2^10, 2^18], avg degree U[4,32] "
+                     "(seed 1), plus 64 sources on R-MAT-22 (seed 2)",
+            "hybrid": hybrid, "clocks": clk}
+
+
+def bench_batch(args, ws, rank, local, torch, abfs, dist):
+    r = measure_batch(args, local, torch, abfs)
+    value, _ = job_throughput(r["total_edges"], r["ms"], dist, "cuda")
     line = {
-        "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": batch_ms, "higher_is_better": True,
+        "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": r["steps"],
+        "warmup": r["warmup"], "ms_per_step": r["ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "batch512_rmat22x64",
-                   "graph": "512 ER/R-MAT graphs, n log-uniform in [2^10, 2^18], avg degree "
-                            "U[4,32] (seed 1), plus 64 sources on R-MAT-22 (seed 2)",
-                   "queries": nq, "step": "one persistent launch (CUDA graph replay) of all queries, "
-                            "parameters from the batch autotuner",
+        "config": {"workload": "batch512_rmat22x64", "graph": r["graph"],
+                   "queries": r["queries"], "step": r["launch"],
                    "l2": "inputs larger than L2 (R-MAT-22 rowidx 513 MB, 576 workspaces)"},
-        "batched": {"ms": batch_ms, "queries_per_s": nq / (batch_ms * 1e-3), "gteps": value,
-                    "single_query_ms": single_ms,
-                    "single_query_gteps": total_edges / (single_ms * 1e-3) / 1e9,
-                    "speedup_vs_single": single_ms / batch_ms, "parts": parts,
-                    "tuned_params": tuned.as_dict(), "tuner_ms": tuned_ms},
-        "hybrid": hybrid,
-        "gpu_launches": 3 * steps, "clocks": clk,
+        "batched": {k: r[k] for k in ("ms", "queries_per_s", "gteps", "single_query_ms",
+                                      "single_query_gteps", "speedup_vs_single", "parts",
+                                      "tuned_params", "tuner_ms")},
+        "hybrid": r["hybrid"],
+        "gpu_launches": 3 * r["steps"], "clocks": r["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def bench_serve(args, ws, rank, local, torch, abfs, dist):
+def measure_serve(args, torch, abfs):
     """32 resident graphs (16 R-MAT of scales 16..22, 15 ER of 2^16..2^20
     vertices, one 2048 x 2048 grid); queries with a uniform graph and source
     (degree >= 1) arrive as a Poisson stream at 0.5, 0.8 and 1.0 x the
-    saturation rate measured first with a closed burst."""
+    saturation rate measured first with a closed burst.  Returns a dict."""
     specs = synth.serve_graph_specs()
     hosts = [synth.make_serve_graph(k, kw) for k, kw in specs]
     graphs = [abfs.graph_create(h.colptr, h.rowidx, directed=False) for h in hosts]
@@ -421,25 +449,45 @@ def bench_serve(args, ws, rank, local, torch, abfs, dist):
     sat = run(0.0, min(nq, 20000))              # closed burst: saturation throughput
     rates = [0.5, 0.8, 1.0]
     per = [run(f * sat["qps"], nq) for f in rates]
-    best = per[-1]
+    for G in graphs:
+        G.destroy()
+    return {"queries_per_rate": nq, "sat": sat, "rates": rates, "per": per,
+            "single_qps": single_qps, "n_single": n_single}
+
+
+def serve_summary(r):
+    """The serving figures of measure_serve's result."""
+    best = r["per"][-1]
+    return {
+        "graph": "32 resident graphs: 16 R-MAT (scales 16..22), 15 ER (2^16..2^20, d=8), "
+                 "one 2048x2048 grid",
+        "queries_per_rate": r["queries_per_rate"],
+        "arrivals": "Poisson at 0.5/0.8/1.0 x saturation",
+        "saturation": {k: r["sat"][k] for k in ("qps", "p50_ms", "p99_ms", "completed", "launches")},
+        "rates": [{k: x[k] for k in ("offered_qps", "qps", "p50_ms", "p99_ms", "mean_ms", "max_ms",
+                                     "completed", "launches", "buffer_waits")} for x in r["per"]],
+        "qps": best["qps"], "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"],
+        "single_query": {"qps": r["single_qps"], "queries": r["n_single"],
+                         "api": "abfs_run per query on one stream"},
+        "speedup_vs_single": r["sat"]["qps"] / r["single_qps"],
+    }
+
+
+def bench_serve(args, ws, rank, local, torch, abfs, dist):
+    r = measure_serve(args, torch, abfs)
+    summ = serve_summary(r)
+    best = r["per"][-1]
     job_qps, _ = job_rate(float(best["completed"]), best["wall_s"] * 1e3, dist, "cuda")
     line = {
         "metric": "queries/s", "value": job_qps, "unit": "queries/s", "n_gpus": ws,
-        "steps": len(rates), "warmup": 1, "ms_per_step": best["wall_s"] * 1e3,
+        "steps": len(r["rates"]), "warmup": 1, "ms_per_step": best["wall_s"] * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "serve32_poisson",
-                   "graph": "32 resident graphs: 16 R-MAT (scales 16..22), 15 ER (2^16..2^20, d=8), "
-                            "one 2048x2048 grid",
-                   "queries_per_rate": nq, "arrivals": "Poisson at 0.5/0.8/1.0 x saturation"},
-        "saturation": {k: sat[k] for k in ("qps", "p50_ms", "p99_ms", "completed", "launches")},
-        "rates": [{k: r[k] for k in ("offered_qps", "qps", "p50_ms", "p99_ms", "mean_ms", "max_ms",
-                                     "completed", "launches", "buffer_waits")} for r in per],
-        "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"],
-        "single_query": {"qps": single_qps, "queries": n_single,
-                         "api": "abfs_run per query on one stream"},
-        "speedup_vs_single": sat["qps"] / single_qps,
+        "config": {"workload": "serve32_poisson", "graph": summ["graph"],
+                   "queries_per_rate": summ["queries_per_rate"], "arrivals": summ["arrivals"]},
     }
+    line.update({k: summ[k] for k in ("saturation", "rates", "p50_ms", "p99_ms", "single_query",
+                                      "speedup_vs_single")})
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -517,6 +565,8 @@ def main():
     ap.add_argument("--shrink", type=float, default=0.0)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch-serve", action="store_true",
+                    help="default workload: skip the 576-query batch and the serving run")
     args = ap.parse_args()
     ws, rank, local = _dist()
 
@@ -745,6 +795,19 @@ def main():
                                "single_query_gteps": sum(bm_c) / (sms * 1e-3) / 1e9,
                                "speedup_vs_single": sms / bms}
             plan.destroy()
+
+    if args.workload == "rmat22" and ws == 1 and not args.no_extras and not args.no_batch_serve:
+        # the batch of 576 queries (512 graphs + 64 R-MAT-22 sources) and the
+        # serving workload, measured in the same run
+        try:
+            line["batched_576"] = measure_batch(args, local, torch, abfs, big=g, G22=G, clocks=False)
+            line["batched_576"].pop("clocks", None)
+        except Exception as exc:
+            line["batched_576"] = {"error": f"{type(exc).__name__}: {exc}"}
+        try:
+            line["serve"] = serve_summary(measure_serve(args, torch, abfs))
+        except Exception as exc:
+            line["serve"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, srcs)
