@@ -105,6 +105,20 @@ typedef struct {
                                  batches; path counts and serving stay top-down.  Submatrix mode without physical
                                  shrink only (else ABFS_ERR_INVALID_ARG). */
     uint32_t bottom_up_beta;  /* see bottom_up_alpha */
+    uint32_t cluster_ctas;    /* CTAs per thread-block cluster of the persistent launch, 1..16
+                                 (1: none).  With clusters, a level small enough for a
+                                 resident narrow run runs instead on the advancing CTA and
+                                 the idle CTAs of its cluster together (a cluster run): the
+                                 frontier list stays in global memory, its counters and the
+                                 per-level barrier live in the leading CTA's shared memory
+                                 (distributed shared memory).  Results are identical. */
+    uint32_t cluster_min;     /* a level of >= this many entry slots starts a cluster run
+                                 (smaller ones run on one CTA; a larger level that a
+                                 single CTA may not take starts one too) */
+    uint32_t cluster_max;     /* a cluster run continues while a level has <= this many
+                                 frontier vertices ... */
+    uint32_t cluster_edges;   /* ... and <= this many entry slots (column entries + 2 per
+                                 vertex) */
 } abfs_params;
 
 /* Per-search counters, filled when a stats pointer is passed. */
@@ -208,8 +222,10 @@ int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_host, int32_t*
  *   5 level claimed by reductions, 6 extraction of its new vertices,
  *   7 frontier bitmap of a bottom-up level, 8 bottom-up level,
  *   0xFE start, 0xFF end), [3] 0 if the phase was published to the whole
- *   grid, 1 if it ran on one CTA, 2 if it is a further level of a resident
- *   narrow run, [4] units or touched rows of the phase, [5] frontier
+ *   grid, 1 if it ran on one CTA (or started a cluster run), 2 if it is a
+ *   further level of a resident narrow run, 3 if it is a further level of a
+ *   cluster run ([4] then holds the run's CTAs), [4] units or touched rows of
+ *   the phase, [5] frontier
  *   vertices, [6] entry slots of that frontier (column entries + 2 per
  *   vertex, low 32 bits), [7] 0.  For a level, [4] is its number of work
  *   units (comparator mask: touched rows).

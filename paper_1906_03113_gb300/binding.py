@@ -49,6 +49,10 @@ class Params(ctypes.Structure):
         ("claim_scan", ctypes.c_uint32),
         ("bottom_up_alpha", ctypes.c_uint32),
         ("bottom_up_beta", ctypes.c_uint32),
+        ("cluster_ctas", ctypes.c_uint32),
+        ("cluster_min", ctypes.c_uint32),
+        ("cluster_max", ctypes.c_uint32),
+        ("cluster_edges", ctypes.c_uint32),
     ]
 
     def as_dict(self) -> dict:

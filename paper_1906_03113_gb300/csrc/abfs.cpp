@@ -128,6 +128,10 @@ abfs_params default_params() {
     p.claim_scan = 1u << 22;
     p.bottom_up_alpha = 0;
     p.bottom_up_beta = 24;
+    p.cluster_ctas = 8;
+    p.cluster_min = 0;
+    p.cluster_max = 16384;
+    p.cluster_edges = 1u << 15;
     return p;
 }
 
@@ -145,6 +149,7 @@ int check_params(const abfs_params& p) {
     if (!(p.shrink_theta >= 0.f) || p.shrink_theta > 1.f) return ABFS_ERR_INVALID_ARG;
     if (p.timeout_ms < 1 || p.timeout_ms > 600000) return ABFS_ERR_INVALID_ARG;
     if (p.narrow_resident > 1) return ABFS_ERR_INVALID_ARG;
+    if (p.cluster_ctas < 1 || p.cluster_ctas > 16) return ABFS_ERR_INVALID_ARG;
     // the hybrid reads the input columns: submatrix mode, no physical shrink
     if (p.bottom_up_alpha && (p.mode != ABFS_MODE_SUBMATRIX || shrink_enabled(p)))
         return ABFS_ERR_INVALID_ARG;
@@ -169,6 +174,10 @@ EngineParams engine_params(const abfs_params& p) {
     e.shrink_tile = kTileMax;
     e.init_tile = 65536;
     e.timeout_ns = (unsigned long long)p.timeout_ms * 1000000ull;
+    e.cluster = p.cluster_ctas;
+    e.cluster_min = p.cluster_min;
+    e.cluster_max = p.cluster_max;
+    e.cluster_edges = p.cluster_edges;
     return e;
 }
 
@@ -262,7 +271,17 @@ int grid_for(int sms, const abfs_params& p) {
     int bps = 0;
     if (engine_occupancy(p.mode, &bps) != cudaSuccess || bps < 1) bps = 1;
     const int per_sm = std::min<int>(bps, (int)p.ctas_per_sm);
-    return std::max(per_sm * std::max(sms, 1), 1);
+    int grid = std::max(per_sm * std::max(sms, 1), 1);
+    const int c = (int)p.cluster_ctas;
+    if (c > 1) {
+        // whole clusters only, and no more than can be resident at once: every
+        // CTA of the persistent launch runs from the start
+        int nc = 0;
+        if (engine_max_clusters(p.mode, (uint32_t)c, &nc) != cudaSuccess || nc < 1) nc = 1;
+        grid = std::min(grid / c, nc) * c;
+        if (grid < c) grid = c;
+    }
+    return grid;
 }
 
 }  // namespace abfs
@@ -889,7 +908,7 @@ std::string params_json(const abfs_params& p) {
       << ",\"narrow_edges\":" << p.narrow_edges
       << ",\"ctas_per_sm\":" << p.ctas_per_sm << ",\"shrink_theta\":" << p.shrink_theta
       << ",\"shrink_max\":" << p.shrink_max << ",\"narrow_resident\":" << p.narrow_resident
-      << ",\"claim_scan\":" << p.claim_scan;
+      << ",\"claim_scan\":" << p.claim_scan << ",\"cluster_ctas\":" << p.cluster_ctas;
     return o.str();
 }
 
@@ -946,6 +965,7 @@ extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count
             if (json_num(found, "shrink_max", &v)) p.shrink_max = (uint32_t)v;
             if (json_num(found, "narrow_resident", &v)) p.narrow_resident = (uint32_t)v;
             if (json_num(found, "claim_scan", &v)) p.claim_scan = (uint32_t)v;
+            if (json_num(found, "cluster_ctas", &v)) p.cluster_ctas = (uint32_t)v;
             p.mode = mode;
             if (check_params(p) == ABFS_OK) {
                 std::lock_guard<std::mutex> lk(g->mu);
@@ -973,6 +993,13 @@ extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count
                 p.ctas_per_sm = cp;
                 cands.push_back(p);
             }
+    // cluster runs of other sizes, and none
+    for (uint32_t cc : {1u, 4u, 16u}) {
+        abfs_params p = default_params();
+        p.mode = mode;
+        p.cluster_ctas = cc;
+        cands.push_back(p);
+    }
     if (mode == ABFS_MODE_SUBMATRIX) {
         const float thetas[] = {0.5f, 0.8f, 0.95f};
         for (float th : thetas) {
@@ -1122,6 +1149,7 @@ extern "C" int abfs_batch_tune(const abfs_graph_t* g, const uint32_t* sources, u
             if (json_num(found, "shrink_max", &v)) p.shrink_max = (uint32_t)v;
             if (json_num(found, "narrow_resident", &v)) p.narrow_resident = (uint32_t)v;
             if (json_num(found, "claim_scan", &v)) p.claim_scan = (uint32_t)v;
+            if (json_num(found, "cluster_ctas", &v)) p.cluster_ctas = (uint32_t)v;
             p.mode = mode;
             if (check_params(p) == ABFS_OK) {
                 if (best) *best = p;
@@ -1135,18 +1163,22 @@ extern "C" int abfs_batch_tune(const abfs_graph_t* g, const uint32_t* sources, u
     const uint32_t granules[] = {512, 1024, 4096};
     const uint32_t narrow_e[] = {16384, 65536};
     const uint32_t scans[] = {0, 1u << 22};
+    // with cluster runs (default cluster size) and without (single-CTA narrow runs)
+    const uint32_t clusters[] = {default_params().cluster_ctas, 1u};
     for (uint32_t ue : granules)
         for (uint32_t ne : narrow_e)
-            for (uint32_t sc : scans) {
-                if (mode == ABFS_MODE_PLAIN && sc) continue;
-                abfs_params p = default_params();
-                p.mode = mode;
-                p.unit_entries = ue;
-                p.narrow_edges = ne;
-                p.narrow_max = ne / 16;
-                p.claim_scan = sc;
-                cands.push_back(p);
-            }
+            for (uint32_t sc : scans)
+                for (uint32_t cc : clusters) {
+                    if (mode == ABFS_MODE_PLAIN && sc) continue;
+                    abfs_params p = default_params();
+                    p.mode = mode;
+                    p.unit_entries = ue;
+                    p.narrow_edges = ne;
+                    p.narrow_max = ne / 16;
+                    p.claim_scan = sc;
+                    p.cluster_ctas = cc;
+                    cands.push_back(p);
+                }
     if (mode == ABFS_MODE_SUBMATRIX) {
         const float thetas[] = {0.5f, 0.8f};
         for (float th : thetas) {

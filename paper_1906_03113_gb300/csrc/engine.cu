@@ -249,21 +249,45 @@ static cudaError_t set_smem_attr() {
                                  pct > 100 ? 100 : pct);
     }
 #endif
+    // clusters of up to 16 CTAs (more than the portable 8)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(engine_kernel<MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess) done = true;
     return e;
 }
 
+// Launch configuration of the persistent engine: `grid` CTAs in clusters of
+// a.p.cluster CTAs (grid is a multiple of it).
+static cudaLaunchConfig_t engine_config(const EngineArgs& a, int grid, cudaStream_t s,
+                                        cudaLaunchAttribute* at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = sizeof(Smem);
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = a.p.cluster < 1 ? 1u : a.p.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
 cudaError_t launch_engine(const EngineArgs& a, int grid, cudaStream_t s) {
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = engine_config(a, grid, s, at);
     cudaError_t e;
     if (a.p.mode == kModePlain) {
         e = set_smem_attr<kModePlain>();
         if (e != cudaSuccess) return e;
-        engine_kernel<kModePlain><<<grid, kThreads, sizeof(Smem), s>>>(a);
+        e = cudaLaunchKernelEx(&cfg, engine_kernel<kModePlain>, a);
     } else {
         e = set_smem_attr<kModeSub>();
         if (e != cudaSuccess) return e;
-        engine_kernel<kModeSub><<<grid, kThreads, sizeof(Smem), s>>>(a);
+        e = cudaLaunchKernelEx(&cfg, engine_kernel<kModeSub>, a);
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -275,6 +299,17 @@ cudaError_t engine_occupancy(uint32_t mode, int* blocks_per_sm) {
                                                              kThreads, sizeof(Smem));
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, engine_kernel<kModeSub>,
                                                          kThreads, sizeof(Smem));
+}
+
+cudaError_t engine_max_clusters(uint32_t mode, uint32_t cluster, int* clusters) {
+    cudaError_t e = (mode == kModePlain) ? set_smem_attr<kModePlain>() : set_smem_attr<kModeSub>();
+    if (e != cudaSuccess) return e;
+    EngineArgs a{};
+    a.p.cluster = cluster;
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = engine_config(a, (int)cluster * 64, nullptr, at);
+    if (mode == kModePlain) return cudaOccupancyMaxActiveClusters(clusters, engine_kernel<kModePlain>, &cfg);
+    return cudaOccupancyMaxActiveClusters(clusters, engine_kernel<kModeSub>, &cfg);
 }
 
 }  // namespace abfs

@@ -62,6 +62,83 @@ __device__ __forceinline__ uint32_t ld_ro(const uint32_t* p) { return __ldg(p); 
 // fence, which orders it after the writes of earlier phases.
 __device__ __forceinline__ uint32_t ld_frozen(const uint32_t* p) { return *p; }
 
+// ---------------------------------------------------------------------------
+// thread-block cluster: distributed shared memory (DSMEM)
+// ---------------------------------------------------------------------------
+// Addresses below are shared::cluster addresses: mapa turns this CTA's
+// shared-memory address of a variable into the address of the same variable
+// in the CTA of rank `rank` of the cluster.  Every launch is a cluster launch
+// (a plain launch is a cluster of one CTA), so these are valid with rank 0 in
+// a launch without clusters.
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t ds_addr(const void* p, uint32_t rank) {
+    const uint32_t la = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+    return ra;
+}
+__device__ __forceinline__ uint32_t ds_ld_acquire(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ds_ld_acquire64(uint32_t a) {
+    unsigned long long v;
+    asm volatile("ld.acquire.cluster.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ds_ld_relaxed(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.relaxed.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void ds_st_release(uint32_t a, uint32_t v) {
+    asm volatile("st.release.cluster.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void ds_st_release64(uint32_t a, unsigned long long v) {
+    asm volatile("st.release.cluster.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ds_add(uint32_t a, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.relaxed.cluster.shared::cluster.add.u32 %0, [%1], %2;"
+                 : "=r"(old) : "r"(a), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void ds_add64(uint32_t a, unsigned long long v) {
+    asm volatile("red.relaxed.cluster.shared::cluster.add.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ void ds_add_release(uint32_t a, uint32_t v) {
+    asm volatile("red.release.cluster.shared::cluster.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ds_cas(uint32_t a, uint32_t cmp, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.relaxed.cluster.shared::cluster.cas.b32 %0, [%1], %2, %3;"
+                 : "=r"(old) : "r"(a), "r"(cmp), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ uint32_t ds_or(uint32_t a, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.relaxed.cluster.shared::cluster.or.b32 %0, [%1], %2;"
+                 : "=r"(old) : "r"(a), "r"(v) : "memory");
+    return old;
+}
+// Every thread of every CTA of the cluster (hardware barrier).  Used only at
+// the start and the end of the kernel, which every CTA reaches.
+__device__ __forceinline__ void cluster_barrier_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+                 ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -98,6 +175,38 @@ struct RanPhase {
     unsigned long long desc;  // [epoch:32][units:32] of the phase
 };
 
+// The cluster mailbox of a CTA.  Peers reach it through DSMEM.
+//
+// A cluster run (engine_cluster.cuh) has no per-level leader step: at the end
+// of every step each member writes a message -- its step tag, the vertices it
+// appended, their entry slots, its error flag -- into its slot of every
+// member's box, then waits on its own box for the others' messages; every
+// member takes the same decision from the same messages.  The leader's box
+// also holds the run's fields and the append counters the members share.
+constexpr int kClusterMax = 16;
+static_assert(kClusterMax <= 16, "a run number keeps the leader's rank in 4 bits");
+// A message is one 64-bit word (one remote store per member):
+// [step + 1 : 15][error : 1][entry slots / 256, saturated : 16][vertices or
+// rows appended : 32].  Members clear their own slots when a run ends, so a
+// tag can only match a message of the current run.
+typedef unsigned long long ClusterMsg;
+struct ClusterBox {
+    uint32_t lock;       // rank 0's copy: 0 = no run in the cluster, else leader rank + 1
+    uint32_t idle;       // 1 while this CTA finds no work (leaders invite idle CTAs only)
+    unsigned long long inv;    // invitation to this CTA: [seq : 32][leader rank + 1 : 32]
+    uint32_t join;       // leader: [seq : 15][closed : 1][member bits : 16]
+    uint32_t ctr[2];     // leader: append positions of the members, by step parity
+    uint32_t seq;        // leader: number of its last run: [count : 28][leader rank : 4]
+    unsigned long long start;  // leader: [seq : 32][1 : 32] once the run's fields are set
+    uint32_t members;    // leader: member bits of the current run
+    uint32_t run_q;      // leader: instance of the run
+    uint32_t run_k;      // leader: first level of the run
+    uint32_t run_f;      // leader: vertices of the first level's list
+    uint32_t run_reached, run_shrinks;     // leader: search counters at the start
+    uint32_t run_sw, run_mcur, run_mprev;  // leader: matrices of the run
+    ClusterMsg msg[2][kClusterMax];        // every box: [step parity][member r]
+};
+
 struct Smem {
     // staged frontier vertices of the unit being expanded: id, column begin
     // minus slot offset (row index of slot s is b[t] + s), slot offset, and
@@ -128,6 +237,15 @@ struct Smem {
     // resident narrow run: list counters and the search's state between levels
     uint32_t nq_cnt, nt_cnt, nr_f, nr_reached, nr_shrinks, nr_stop, nr_sw, nr_mcur, nr_mprev;
     unsigned long long nq_slots;
+    // cluster run: shared::cluster address of the leader's append counter of
+    // the current step (positions in the list / touched rows); 0 outside runs.
+    // The member's own appends are still counted in nq_cnt / nt_cnt / nq_slots.
+    uint32_t ds_ctr;
+    // cluster run state of this CTA: leader rank, run sequence, members, step
+    // decision (stop flag and the next step's items), idle peers seen
+    uint32_t cr_leader, cr_seq, cr_join, cr_stop, cr_f, cr_idle, cr_base;
+    unsigned long long cr_slots;
+    ClusterBox cbox;
     Cmd cmd;
     RanPhase ran;
     Inst I;
@@ -136,6 +254,16 @@ struct Smem {
     uint32_t idle_exit;
     unsigned long long prof[kProfSlots];
 };
+
+// Warp 0: the other CTAs of the cluster that report themselves idle (a hint:
+// they may take work before they see an invitation), as bits, to every lane.
+__device__ __forceinline__ uint32_t cluster_idle_peers(Smem& sm) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t C = cluster_size(), me = cluster_rank();
+    bool idle = false;
+    if (lane < C && lane != me) idle = ds_ld_relaxed(ds_addr(&sm.cbox.idle, lane)) != 0u;
+    return __ballot_sync(0xFFFFFFFFu, idle);
+}
 
 // Profiling runs: thread 0 adds the cycles since t0 to slot `slot`.
 __device__ __forceinline__ long long prof_now(const Smem& sm) {

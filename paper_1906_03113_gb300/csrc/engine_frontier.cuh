@@ -234,14 +234,20 @@ __device__ ABFS_NOINLINE void cta_flush(Smem& sm, const Inst& I, InstCtl* ctl,
 
 // Resident narrow runs: a warp appends its n staged vertices to the frontier
 // list of parity pn (vertex, column begin, column length in matrix mat_next),
-// at a position taken from a shared-memory counter.  Whole warp.
+// at a position taken from a shared-memory counter (in a cluster run, the
+// leader CTA's counter, reached through DSMEM).  Whole warp.
 __device__ __forceinline__ void narrow_append(Smem& sm, const Inst& I, InstCtl* ctl, uint32_t pn, uint32_t mat_next,
                               uint32_t& wc) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t n = wc;
     const uint32_t* wv = sm.wv[threadIdx.x >> 5];
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&sm.nq_cnt, n);
+    // positions: this CTA's own counter, or in a cluster run the leader's
+    // (DSMEM); the CTA's own counter always counts its appends
+    if (lane == 0) {
+        base = atomicAdd(&sm.nq_cnt, n);
+        if (sm.ds_ctr) base = ds_add(sm.ds_ctr, n);
+    }
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     uint32_t wsum = 0;
     for (uint32_t i0 = 0; i0 < n; i0 += 32 * kIlp) {
@@ -282,13 +288,17 @@ __device__ __forceinline__ void narrow_append(Smem& sm, const Inst& I, InstCtl* 
 }
 
 // Resident narrow runs of the comparator: a warp appends its n staged
-// first-touched rows to the touched list.  Whole warp.
+// first-touched rows to the touched list (counter as in narrow_append).
+// Whole warp.
 __device__ __forceinline__ void narrow_touch(Smem& sm, const Inst& I, InstCtl* ctl, uint32_t& wc) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t n = wc;
     const uint32_t* wv = sm.wv[threadIdx.x >> 5];
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&sm.nt_cnt, n);
+    if (lane == 0) {
+        base = atomicAdd(&sm.nt_cnt, n);
+        if (sm.ds_ctr) base = ds_add(sm.ds_ctr, n);
+    }
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     for (uint32_t i = lane; i < n; i += 32) {
         const uint32_t at = base + i;

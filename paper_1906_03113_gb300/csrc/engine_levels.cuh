@@ -1,5 +1,5 @@
-// Phase control: running a unit, resident narrow runs, choosing and publishing
-// the next phase of a search.
+// Phase control: running a unit, and resident narrow runs of small levels on
+// one CTA.
 // Part of the persistent engine (engine.cu), split by topic; included in order.
 #pragma once
 
@@ -75,24 +75,25 @@ __device__ __forceinline__ bool shrink_due(const EngineParams& P, uint32_t reach
 // last frontier is then rewritten as blocks and the general path decides what
 // follows.
 
-// Expands the f vertices of the level-k list (lens: fbeg/fpre hold column
-// begins and lengths in matrix mat; otherwise only the ids are valid and the
-// columns are looked up) in chunks of up to `tile` vertices and windows of up
-// to kUnitMax slots.  Whole CTA.
+// Expands the f vertices at [base, base + f) of the level-k list (lens:
+// fbeg/fpre hold column begins and lengths in matrix mat; otherwise only the
+// ids are valid and the columns are looked up) in chunks of up to `tile`
+// vertices and windows of up to kUnitMax slots.  Whole CTA.
 template <int MODE>
 __device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                              uint32_t k, uint32_t f, bool lens, uint32_t mat, uint32_t mat_next,
-                              Tally& t, uint32_t& nnz_local) {
+                              uint32_t k, uint32_t base, uint32_t f, bool lens, uint32_t mat,
+                              uint32_t mat_next, Tally& t, uint32_t& nnz_local) {
     const uint32_t p = k & 1;
     for (uint32_t c0 = 0; c0 < f; c0 += P.tile) {
         const long long pt0 = prof_now(sm);
         const uint32_t cnt = min(P.tile, f - c0);
         for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
-            const uint32_t v = ld_l2(I.fq[p] + c0 + s);
+            const uint32_t at = base + c0 + s;
+            const uint32_t v = ld_l2(I.fq[p] + at);
             uint32_t beg, len;
             if (lens) {
-                beg = ld_l2(I.fbeg[p] + c0 + s);
-                len = ld_l2(I.fpre[p] + c0 + s);
+                beg = ld_l2(I.fbeg[p] + at);
+                len = ld_l2(I.fpre[p] + at);
             } else {
                 const ColRef c = col_of(I, mat, v);
                 beg = c.beg;
@@ -140,6 +141,152 @@ __device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const
             __syncthreads();
         }
     }
+}
+
+// Short columns: a list slice of at most kThreads vertices whose columns all
+// hold at most kShortCol entries is expanded one vertex per thread, with all
+// of a vertex's row loads, mask tests and claims in flight together and no CTA
+// barrier inside; the column of a row that passes the mask is looked up while
+// its claim is in flight, so a claimed vertex is appended without a further
+// round trip.  Submatrix mode appends the vertices of level k+1 to the next
+// list; the comparator multiplies every entry into the stamped accumulator and
+// appends first-touched rows to the touched list.  Returns false, having
+// changed nothing, when the slice does not qualify (the caller then uses
+// narrow_expand).  Whole CTA.
+constexpr uint32_t kShortCol = 4;
+
+template <int MODE>
+__device__ ABFS_NOINLINE bool narrow_expand_short(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                                  Smem& sm, uint32_t k, uint32_t base, uint32_t f,
+                                                  bool lens, uint32_t mat, uint32_t mat_next,
+                                                  Tally& t, uint32_t& nnz_local) {
+    if (f > (uint32_t)kThreads) return false;
+    const uint32_t p = k & 1, pn = p ^ 1;
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    const bool have = tid < f;
+    uint32_t v = 0, beg = 0, len = 0;
+    if (have) {
+        const uint32_t at = base + tid;
+        v = ld_l2(I.fq[p] + at);
+        if (lens) {
+            beg = ld_l2(I.fbeg[p] + at);
+            len = ld_l2(I.fpre[p] + at);
+        } else {
+            const ColRef c = col_of(I, mat, v);
+            beg = c.beg;
+            len = c.len;
+        }
+    }
+    if (__syncthreads_or(have && len > kShortCol)) return false;
+    const uint32_t* rows = rows_of(I, mat);
+    const uint64_t pol = evict_first_policy();
+    uint32_t r[kShortCol];
+#pragma unroll
+    for (uint32_t j = 0; j < kShortCol; ++j)
+        r[j] = (have && j < len) ? ld_row(rows, beg + j, mat, pol) : kUnset;
+    if (have) {
+        // the frontier joins the visited set of the next level's test
+        if (MODE == kModeSub) atomicOr(I.bm[pn] + (v >> 5), 1u << (v & 31));
+        nnz_local += (mat == 0) ? len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
+        t.read += len;
+    }
+    uint32_t won = 0;  // bit j: entry j claimed (submatrix) / first touch (comparator)
+    uint32_t nb[kShortCol], nl[kShortCol];
+    if (MODE == kModeSub) {
+        const uint32_t* test_bm = I.bm[p];
+        unsigned long long* const sigma = I.sigma;
+        const unsigned long long sv = (sigma && have) ? ld_l2(sigma + v) : 0ull;
+        uint32_t w[kShortCol];
+#pragma unroll
+        for (uint32_t j = 0; j < kShortCol; ++j)
+            w[j] = r[j] != kUnset ? ld_l2(test_bm + (r[j] >> 5)) : 0xFFFFFFFFu;
+        uint32_t old[kShortCol];
+#pragma unroll
+        for (uint32_t j = 0; j < kShortCol; ++j) {
+            old[j] = 0;
+            nb[j] = 0;
+            nl[j] = 0;
+            if (!((w[j] >> (r[j] & 31)) & 1u)) {
+                ++t.unmasked;
+                ++t.claims;
+                old[j] = atomicMin(I.parent + r[j], v);
+                const ColRef c = col_of(I, mat_next, r[j]);
+                nb[j] = c.beg;
+                nl[j] = c.len;
+                if (sigma) atomicAdd(sigma + r[j], sv);
+            }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kShortCol; ++j) {
+            if (!((w[j] >> (r[j] & 31)) & 1u) && old[j] == kUnset) {
+                won |= 1u << j;
+                I.level[r[j]] = (int32_t)(k + 1);
+                atomicOr(I.bm[pn] + (r[j] >> 5), 1u << (r[j] & 31));
+            }
+        }
+    } else {
+#pragma unroll
+        for (uint32_t j = 0; j < kShortCol; ++j) {
+            nb[j] = 0;
+            nl[j] = 0;
+            if (r[j] != kUnset) {
+                ++t.unmasked;
+                ++t.claims;
+                const unsigned long long o = atomicMin(I.y + r[j], plain_key(k, v));
+                if ((uint32_t)(o >> 32) != plain_stamp(k)) won |= 1u << j;
+            }
+        }
+    }
+    // positions: each warp reserves its entries in this CTA's counter; in a
+    // cluster run the CTA then reserves its total in the leader's counter with
+    // one DSMEM atomic (not one per warp: they would queue at one address)
+    const uint32_t cnt = __popc(won);
+    const uint32_t incl = warp_incl_scan(cnt);
+    const uint32_t wtot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    uint32_t woff = 0;
+    if (lane == 31 && wtot) woff = atomicAdd(MODE == kModeSub ? &sm.nq_cnt : &sm.nt_cnt, wtot);
+    woff = __shfl_sync(0xFFFFFFFFu, woff, 31);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t tot = MODE == kModeSub ? sm.nq_cnt : sm.nt_cnt;
+        sm.cr_base = (sm.ds_ctr && tot) ? ds_add(sm.ds_ctr, tot) : 0u;
+    }
+    __syncthreads();
+    if (wtot) {
+        uint32_t at = sm.cr_base + woff + incl - cnt;
+        uint32_t slots = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < kShortCol; ++j) {
+            if ((won >> j) & 1u) {
+                if (at < I.n) {
+                    if (MODE == kModeSub) {
+                        I.fq[pn][at] = r[j];
+                        I.fbeg[pn][at] = nb[j];
+                        I.fpre[pn][at] = nl[j];
+                        slots += nl[j] + kVertexSlots;
+                        // the next level reads this column: start bringing it to L2
+                        if (nl[j]) {
+                            const uint32_t* c = rows_of(I, mat_next) + nb[j];
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(c));
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(c + nl[j] - 1));
+                        }
+                    } else {
+                        I.touched[at] = r[j];
+                    }
+                } else {
+                    fail(ctl, 7 /* ABFS_ERR_DEVICE */);
+                }
+                ++at;
+            }
+        }
+        if (MODE == kModeSub) {
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) slots += __shfl_xor_sync(0xFFFFFFFFu, slots, d);
+            if (lane == 0 && slots) atomicAdd(&sm.nq_slots, (unsigned long long)slots);
+        }
+    }
+    __syncthreads();
+    return true;
 }
 
 // Rewrites the list of parity pn (fn vertices; fpre holds column lengths) as
@@ -243,7 +390,8 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
         const uint32_t mat_next = k + 1 >= sw ? mat_cur : mat_prev;
         // issued now, read when the level ends
         const uint32_t err = threadIdx.x == 0 ? ld_relaxed(&ctl->err) : 0u;
-        narrow_expand<MODE>(I, ctl, P, sm, k, f, lens, mat, mat_next, t, nnz_local);
+        if (!narrow_expand_short<MODE>(I, ctl, P, sm, k, 0u, f, lens, mat, mat_next, t, nnz_local))
+            narrow_expand<MODE>(I, ctl, P, sm, k, 0u, f, lens, mat, mat_next, t, nnz_local);
         const long long pt2 = prof_now(sm);
         {
             // the warps' leftovers
@@ -281,6 +429,16 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
         }
         const long long pt3 = prof_now(sm);
         prof_add(sm, kProfNAppend, pt2);
+        if (P.cluster > 1 && threadIdx.x < 32) {
+            // a level big enough for a cluster run ends this run when idle CTAs
+            // of the cluster could take it together
+            const unsigned long long sl = sm.nq_slots;
+            const uint32_t fn = sm.nq_cnt;
+            uint32_t idle = 0;
+            if (sl >= P.cluster_min && sl <= P.cluster_edges && fn <= P.cluster_max)
+                idle = cluster_idle_peers(sm);
+            if (threadIdx.x == 0) sm.cr_idle = idle;
+        }
         if (threadIdx.x == 0) {
             const uint32_t fn = sm.nq_cnt;
             const unsigned long long slots = sm.nq_slots;
@@ -291,6 +449,8 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
             if (fn == 0 || err != 0 || fn > P.narrow_max || slots > P.narrow_edges || guard <= 1)
                 stop = 1;
             else if (MODE == kModeSub && shrink_due(P, sm.nr_reached + fn, I.n, sm.nr_shrinks))
+                stop = 1;
+            else if (P.cluster > 1 && sm.cr_idle)
                 stop = 1;
             if (!stop) {
                 sm.nr_reached += fn;
@@ -319,244 +479,6 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
     stats_flush(sm, ctl);
     prof_add(sm, kProfNBlocks, pt4);
     return k;
-}
-
-// Thread 0 of the advancing CTA: the phase that follows (kind, k), written to
-// sm.cmd; sm.cmd.quit = 1 when the search is over.
-template <int MODE>
-__device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                            uint32_t kind, uint32_t k, uint32_t* done_count) {
-    uint32_t nkind = 0, nk = 0, ni = 0, finish = 0;
-    if (kind == kPhInit) {
-        // the outputs are clear: the source forms the frontier of level 0
-        // (Algorithm 1's V_2 := V_1 \ supp(x_1))
-        const uint32_t s = I.src;
-        I.level[s] = 0;
-        I.parent[s] = s;
-        if (I.sigma) I.sigma[s] = 1ull;
-        if (MODE == kModeSub) atomicOr(I.bm[0] + (s >> 5), 1u << (s & 31));
-        const uint32_t b0 = ld_ro(I.colptr + s);
-        const uint32_t w = ld_ro(I.colptr + s + 1) - b0 + kVertexSlots;
-        I.fq[0][0] = s;
-        I.fbeg[0][0] = b0;
-        I.fpre[0][0] = 0;
-        I.blk[0][0].vb = 0;
-        I.blk[0][0].nv = 1;
-        I.blk[0][0].eb = 0;
-        for (unsigned long long x = 0; x < w; x += P.unit) I.ustart[0][x / P.unit] = make_uint2(0, 0);
-        st_relaxed64(&ctl->bctr[0], ((unsigned long long)w << kBlockBits) | 1ull);
-        st_relaxed(&ctl->fcnt[0], 1u);
-        st_relaxed(&ctl->reached, 1u);
-        nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
-        nk = 0;
-    } else if (kind == kPhStart) {
-        // the frontier of level 0 (the source) was set up before the launch
-        nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
-        nk = 0;
-    } else if (kind == kPhLevelScan) {
-        // the new vertices of a level claimed by reductions are read off the bitmaps
-        nkind = kPhExtract;
-        nk = k;
-    } else if (kind == kPhBuPrep) {
-        nkind = kPhBottomUp;
-        nk = k;
-    } else if (kind == kPhPlainMult) {
-        // comparator: the mask phase of the same level follows the multiply
-        const uint32_t t = ld_relaxed(&ctl->tcnt);
-        nkind = kPhPlainMask;
-        nk = k;
-        ni = t;
-        if (t == 0) {
-            finish = 1;
-            st_relaxed(&ctl->levels, k + 1);
-        }
-    } else {
-        // the frontier of level k+1 is complete (after a level, or after a shrink)
-        const uint32_t pn = (k + 1) & 1, pc = k & 1;
-        const uint32_t nf = ld_relaxed(&ctl->fcnt[pn]);
-        uint32_t reached = ld_relaxed(&ctl->reached);
-        uint32_t shrinks = ld_relaxed(&ctl->shrinks);
-        if (kind != kPhShrink) {
-            st_relaxed(&ctl->levels, k + 1);
-            if (nf == 0) {
-                finish = 1;
-            } else {
-                reached += nf;
-                st_relaxed(&ctl->reached, reached);
-                // the buffers of level k become the "next" buffers of level k+1
-                st_relaxed(&ctl->fcnt[pc], 0u);
-                st_relaxed64(&ctl->bctr[pc], 0ull);
-                if (MODE == kModePlain) st_relaxed(&ctl->tcnt, 0u);
-            }
-        } else {
-            // the copy just written serves the levels from k+2 on
-            const uint32_t dst = sm.cmd.nitems;
-            st_relaxed(&ctl->mat_prev, ld_relaxed(&ctl->mat_cur));
-            st_relaxed(&ctl->mat_cur, dst);
-            st_relaxed(&ctl->mat_switch, k + 2);
-            shrinks += 1;
-            st_relaxed(&ctl->shrinks, shrinks);
-        }
-        if (!finish) {
-            const bool do_shrink =
-                MODE == kModeSub && kind != kPhShrink && shrink_due(P, reached, I.n, shrinks);
-            if (do_shrink) {
-                // alternate copies so the frontier of level k+1 keeps its matrix
-                const uint32_t cur = ld_relaxed(&ctl->mat_cur);
-                nkind = kPhShrink;
-                nk = k;
-                ni = (cur == 1) ? 2u : 1u;
-                st_relaxed(&ctl->shrink_out, 0u);
-            } else {
-                nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
-                nk = k + 1;
-                if (MODE == kModeSub && P.bu_alpha && I.bu_ok && kind != kPhShrink) {
-                    // hybrid direction choice from the frontier's edges m_f and the
-                    // edges of vertices not reached yet m_u: bottom-up once
-                    // m_f * alpha > m_u, back to top-down once n_f * beta < n
-                    const unsigned long long ne1 = ld_relaxed64(&ctl->bctr[pn]) >> kBlockBits;
-                    const unsigned long long mf = ne1 - (unsigned long long)kVertexSlots * nf;
-                    const unsigned long long seen = ld_relaxed64(&ctl->nnz_reached) + mf;
-                    const unsigned long long nnz = ld_ro(I.colptr + I.n);
-                    const unsigned long long mu = nnz > seen ? nnz - seen : 0ull;
-                    uint32_t bu = ld_relaxed(&ctl->bu_on);
-                    bu = bu ? ((unsigned long long)nf * P.bu_beta >= I.n)
-                            : (mf * (unsigned long long)P.bu_alpha > mu);
-                    st_relaxed(&ctl->bu_on, bu);
-                    if (bu) {
-                        // the frontier's columns are never expanded: count them here
-                        atomicAdd(&ctl->nnz_reached, mf);
-                        nkind = (kind == kPhExtract || kind == kPhBottomUp) ? kPhBottomUp : kPhBuPrep;
-                    }
-                }
-            }
-        }
-    }
-    if (ld_relaxed(&ctl->err) != 0) finish = 1;
-    sm.cmd.kind = nkind;
-    sm.cmd.level = nk;
-    sm.cmd.nitems = ni;
-    sm.cmd.quit = finish;
-    if (finish) {
-        const uint32_t e = ld_relaxed(&ctl->err);
-        __threadfence();
-        if (atomicCAS(&ctl->status, (uint32_t)kRunning, e ? (uint32_t)kFailed : (uint32_t)kDone) ==
-            kRunning) {
-            atomicAdd(done_count, 1u);
-            if (I.notify) {
-                // serving: the ticket and status reach the host's mapped word after
-                // every write of the search
-                __threadfence_system();
-                const unsigned long long word = (I.ticket << 8) | (unsigned long long)(e & 0xFFu);
-                asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(I.notify), "l"(word)
-                             : "memory");
-            }
-        }
-    }
-}
-
-// Called by the whole CTA that completed the last unit of phase (kind, k).
-// Runs small follow-up phases alone ("narrow") and publishes large ones.
-template <int MODE>
-__device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
-                        uint32_t kind, uint32_t k, uint32_t* done_count,
-                        unsigned long long* heartbeat) {
-    // the search's phase counter: written only by the advancing CTA, visible
-    // here since this CTA took a unit of the current phase
-    const uint32_t epoch0 = threadIdx.x == 0 ? ld_relaxed(&ctl->epoch) : 0u;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            __threadfence();
-            decide_next<MODE>(I, ctl, P, sm, kind, k, done_count);
-            atomicAdd(heartbeat, 1ull);
-        }
-        __syncthreads();
-        if (sm.cmd.quit) {
-            if (I.trace && threadIdx.x == 0) trace_put(I, ctl, 0xFFu, k, 0u, 0u, 0u, 0ull);
-            return;
-        }
-        const uint32_t nk = sm.cmd.level;
-        uint32_t nkind = sm.cmd.kind;
-        uint32_t ni = sm.cmd.nitems;
-        uint32_t units, nf = 0;
-        unsigned long long ne = 0;
-        bool alone;
-        if (nkind == kPhShrink) {
-            units = (I.n + P.shrink_tile - 1) / P.shrink_tile;
-            alone = units <= 1;
-        } else if (nkind == kPhPlainMask) {
-            units = (ni + P.tile - 1) / P.tile;
-            alone = ni <= P.narrow_max;
-        } else if (nkind == kPhExtract || nkind == kPhBuPrep || nkind == kPhBottomUp) {
-            // runs of 8-word chunks, about two units per CTA (ni = chunks per unit)
-            const uint32_t chunks = (I.nwords + kChunkWords - 1) / kChunkWords;
-            const uint32_t two = 2u * gridDim.x;
-            ni = max((chunks + two - 1) / two, (uint32_t)kWarps);
-            units = (chunks + ni - 1) / ni;
-            alone = units <= 1;
-        } else {
-            // a level (or the comparator's multiply) over the frontier of level nk;
-            // its units are m granules, about two per CTA of the grid (ni = m)
-            ne = ld_relaxed64(&ctl->bctr[nk & 1]) >> kBlockBits;
-            nf = ld_relaxed(&ctl->fcnt[nk & 1]);
-            const unsigned long long mmax = kUnitMax / P.unit;
-            // at most two units per CTA: a third round for a few CTAs would
-            // stretch the level by half
-            const unsigned long long per2 = (unsigned long long)P.unit * 2ull * gridDim.x;
-            unsigned long long m = (ne + per2 - 1) / per2;
-            m = m < 1ull ? 1ull : (m > mmax ? mmax : m);
-            ni = (uint32_t)m;
-            units = (uint32_t)((ne + P.unit * m - 1) / (P.unit * m));
-            alone = nf <= P.narrow_max && ne <= P.narrow_edges;
-            // a large level claims by reductions and a bitmap scan
-            if (MODE == kModeSub && nkind == kPhLevel && !alone && P.scan_min && ne >= P.scan_min)
-                nkind = kPhLevelScan;
-        }
-        if (I.trace && threadIdx.x == 0)
-            trace_put(I, ctl, nkind, nk, alone, nkind == kPhPlainMask ? ni : units, nf, ne);
-        if (!alone) {
-            if (threadIdx.x == 0) {
-                const uint32_t e = epoch0 + 1;
-                const uint32_t q = e & 1;
-                const unsigned long long d = ((unsigned long long)e << 32) | units;
-                st_relaxed(&ctl->kind[q], nkind);
-                st_relaxed(&ctl->plevel[q], nk);
-                st_relaxed(&ctl->nitems[q], ni);
-                st_relaxed(&ctl->pending[q], units);
-                st_relaxed(&ctl->epoch, e);
-                atomicAdd(&ctl->wide_levels, 1u);
-                st_relaxed64(&ctl->desc[q], d);
-                // the phase becomes takeable only after all of the above
-                st_release64(&ctl->grab, (unsigned long long)e << 32);
-                // this CTA knows the phase it published: its first take needs
-                // neither a poll nor a second acquire
-                sm.ran.valid = 1;
-                sm.ran.fresh = 1;
-                sm.ran.q = sm.cmd.q;
-                sm.ran.epoch = e;
-                sm.ran.kind = nkind;
-                sm.ran.level = nk;
-                sm.ran.nitems = ni;
-                sm.ran.desc = d;
-            }
-            __syncthreads();
-            return;
-        }
-        if (P.narrow_loop && (nkind == kPhLevel || nkind == kPhPlainMult)) {
-            // a resident run of narrow levels on this CTA
-            k = narrow_run<MODE>(I, ctl, P, sm, nk, heartbeat);
-            kind = kPhLevel;
-            __threadfence();
-            __syncthreads();
-            continue;
-        }
-        // narrow: this CTA runs every unit of the phase, then decides again
-        for (uint32_t u = 0; u < units; ++u) run_unit<MODE>(I, ctl, P, sm, nkind, nk, u, ni);
-        __threadfence();
-        __syncthreads();
-        kind = nkind;
-        k = nk;
-    }
 }
 
 }  // namespace abfs

@@ -3,7 +3,7 @@
 // Part of the persistent engine (engine.cu), split by topic; included in order.
 #pragma once
 
-#include "engine_levels.cuh"
+#include "engine_advance.cuh"
 
 namespace abfs {
 
@@ -133,7 +133,14 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
     if (threadIdx.x < 32) {
         const uint32_t lane = threadIdx.x;
         bool got = false;
-        if (sm.ran.valid && sm.ran.fresh) {
+        // an invitation to a cluster run comes before any unit
+        uint32_t joined = 0;
+        if (a.p.cluster > 1 && lane == 0) joined = cluster_take_invitation(sm);
+        joined = __shfl_sync(0xFFFFFFFFu, joined, 0);
+        if (joined) {
+            if (lane == 0) sm.cmd.has = 2;
+            __syncwarp();
+        } else if (sm.ran.valid && sm.ran.fresh) {
             // right after a unit that did not end its phase, first try that
             // phase again without polling (an idle CTA polls instead)
             bool ok = false;
@@ -143,7 +150,7 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
             }
             got = __shfl_sync(0xFFFFFFFFu, ok, 0);
         }
-        for (uint32_t base = 0; base < a.ninst && !got; base += 32) {
+        for (uint32_t base = 0; base < a.ninst && !got && !joined; base += 32) {
             const uint32_t idx = base + lane;
             const uint32_t q = (cursor + idx) % a.ninst;
             uint32_t e_seen = 0;
@@ -159,7 +166,9 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
             }
         }
         __syncwarp();
-        if (lane == 0) sm.cmd.has = got;
+        if (lane == 0 && !joined) sm.cmd.has = got;
+        // busy from now on: leaders of cluster runs do not wait for this CTA
+        if (lane == 0 && (got || joined) && a.p.cluster > 1) *(volatile uint32_t*)&sm.cbox.idle = 0u;
         __syncwarp();
         // serving slots are reused by new searches: always reload their descriptor
         if (got && (a.serve || sm.cur_q != sm.cmd.q)) {
@@ -171,6 +180,10 @@ __device__ bool find_and_run(const EngineArgs& a, Smem& sm, uint32_t& cursor) {
     }
     __syncthreads();
     if (!sm.cmd.has) return false;
+    if (sm.cmd.has == 2) {
+        cluster_member_run<MODE>(a, sm);
+        return true;
+    }
     if (sm.cmd.start) {
         start_search(a, sm);
         return true;
@@ -214,8 +227,16 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) engine_kernel(EngineArgs a
         sm.cur_q = kUnset;
         sm.ran.valid = 0;
         sm.ran.fresh = 0;
+        sm.ds_ctr = 0;
+        sm.cr_join = 0;
+        uint32_t* cb = reinterpret_cast<uint32_t*>(&sm.cbox);
+        for (uint32_t w = 0; w < sizeof(ClusterBox) / 4; ++w) cb[w] = 0u;
     }
     __syncthreads();
+    // peers reach this CTA's box only after every CTA of the cluster has
+    // cleared its own
+    const bool clustered = cluster_size() > 1;
+    if (clustered) cluster_barrier_all();
     uint32_t cursor = blockIdx.x % a.ninst;
     uint64_t idle_since = globaltimer();
     unsigned long long last_beat = ~0ull;
@@ -228,9 +249,12 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) engine_kernel(EngineArgs a
         if (sm.cmd.quit) break;
         const long long pti = prof_now(sm);
         if (find_and_run<MODE>(a, sm, cursor)) {
+            if (clustered && threadIdx.x == 0) *(volatile uint32_t*)&sm.cbox.idle = 0u;
             backoff = 64;
             continue;
         }
+        // leaders of cluster runs invite CTAs that find no work
+        if (clustered && threadIdx.x == 0) *(volatile uint32_t*)&sm.cbox.idle = 1u;
         // nothing to take: wait, bounded by the time limit without progress
         if (threadIdx.x == 0) {
             const unsigned long long beat = ld_relaxed64(a.heartbeat);
@@ -251,7 +275,15 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) engine_kernel(EngineArgs a
                     }
                 }
             }
-            __nanosleep(backoff);
+            if (clustered) {
+                // short naps that end as soon as a cluster run invites this CTA
+                for (uint32_t slept = 0; slept < backoff; slept += 128) {
+                    if (*(volatile const unsigned long long*)&sm.cbox.inv) break;
+                    __nanosleep(128);
+                }
+            } else {
+                __nanosleep(backoff);
+            }
             if (backoff < kIdleBackoffMaxNs) backoff <<= 1;
         }
         __syncthreads();
@@ -259,6 +291,11 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) engine_kernel(EngineArgs a
     }
     if (a.prof && threadIdx.x == 0)
         for (int q = 0; q < kProfSlots; ++q) atomicAdd(a.prof + q, sm.prof[q]);
+    // no CTA leaves while a peer may still reach its shared memory
+    if (clustered) {
+        if (threadIdx.x == 0) *(volatile uint32_t*)&sm.cbox.idle = 0u;
+        cluster_barrier_all();
+    }
 }
 
 }  // namespace abfs

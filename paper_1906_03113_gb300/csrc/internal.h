@@ -177,6 +177,10 @@ struct EngineParams {
     uint32_t shrink_tile;          // vertices per shrink unit
     uint32_t init_tile;            // serving: vertices per initialisation unit
     unsigned long long timeout_ns;
+    uint32_t cluster;              // CTAs per thread-block cluster of the launch (1: no cluster runs)
+    uint32_t cluster_min;          // a level of >= cluster_min entry slots starts a cluster run
+    uint32_t cluster_max;          // cluster runs continue while a level has <= cluster_max vertices ...
+    uint32_t cluster_edges;        // ... and <= cluster_edges entry slots
 };
 
 struct EngineArgs {
@@ -258,6 +262,8 @@ cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t*
 cudaError_t launch_init(const EngineArgs& a, uint32_t max_n, cudaStream_t s);
 cudaError_t launch_engine(const EngineArgs& a, int grid, cudaStream_t s);
 cudaError_t engine_occupancy(uint32_t mode, int* blocks_per_sm);
+// Clusters of `cluster` CTAs of the engine that can be resident at once.
+cudaError_t engine_max_clusters(uint32_t mode, uint32_t cluster, int* clusters);
 size_t engine_smem_bytes();
 
 }  // namespace abfs

@@ -88,6 +88,31 @@ MODES = [
                              narrow_max=0, narrow_edges=0)),
 ]
 
+# cluster runs: none (single-CTA narrow runs), other cluster sizes, whole
+# searches in cluster runs, frequent run <-> wide transitions, the comparator's
+# two steps per level, shrinks ending runs, several chunks per member
+MODES += [
+    ("sub_no_cluster", dict(mode=SUB, cluster_ctas=1)),
+    ("plain_no_cluster", dict(mode=PLAIN, cluster_ctas=1)),
+    ("sub_cluster2", dict(mode=SUB, cluster_ctas=2)),
+    ("sub_cluster4_all", dict(mode=SUB, cluster_ctas=4, cluster_min=0, cluster_max=1 << 30,
+                              cluster_edges=1 << 30)),
+    ("sub_cluster8_all", dict(mode=SUB, cluster_ctas=8, cluster_min=0, cluster_max=1 << 30,
+                              cluster_edges=1 << 30)),
+    ("sub_cluster16_all", dict(mode=SUB, cluster_ctas=16, cluster_min=0, cluster_max=1 << 30,
+                               cluster_edges=1 << 30)),
+    ("plain_cluster_all", dict(mode=PLAIN, cluster_min=0, cluster_max=1 << 30,
+                               cluster_edges=1 << 30)),
+    ("sub_cluster_mixed", dict(mode=SUB, cluster_min=64, cluster_max=300, cluster_edges=3000,
+                               narrow_max=40, narrow_edges=400, unit_entries=512)),
+    ("plain_cluster_mixed", dict(mode=PLAIN, cluster_min=64, cluster_max=300, cluster_edges=3000,
+                                 narrow_max=40, narrow_edges=400)),
+    ("sub_cluster_shrink", dict(mode=SUB, tile=64, cluster_min=0, cluster_max=1 << 30,
+                                cluster_edges=1 << 30, shrink_theta=0.05, shrink_max=20)),
+    ("sub_cluster_small_tile", dict(mode=SUB, tile=32, cluster_min=0, cluster_max=1 << 30,
+                                    cluster_edges=1 << 30)),
+]
+
 HYBRID = ("sub_hybrid", "sub_hybrid_always", "sub_hybrid_alternate", "sub_hybrid_scan")
 
 
@@ -343,6 +368,32 @@ def test_hybrid_runs_bottom_up_only_where_allowed():
     D.destroy()
 
 
+def test_cluster_runs_take_the_thin_levels():
+    """A thin search (a 300 x 200 grid from a corner) runs its levels in
+    cluster runs when the launch has clusters (trace entries marked 3, with the
+    run's CTA count), and in single-CTA narrow runs without; both exact."""
+    g = synth.grid(300, 200)
+    G = abfs.graph_create(g.colptr, g.rowidx, directed=False)
+    level, parent, trace = abfs.run_trace(G, 0, params=_params(cluster_min=256), cap=1 << 14)
+    runs = [r for r in trace if r.get("alone") == 3]
+    assert len(runs) > 100 and all(2 <= r["items"] <= 16 for r in runs)
+    _check(g, 0, level, parent, "cluster runs")
+    level, parent, trace = abfs.run_trace(G, 0, params=_params(cluster_ctas=1, cluster_min=256),
+                                          cap=1 << 14)
+    assert not [r for r in trace if r.get("alone") == 3]
+    _check(g, 0, level, parent, "no clusters")
+    G.destroy()
+
+
+def test_cluster_parameter_rules():
+    G = abfs.graph_create(*(lambda g: (g.colptr, g.rowidx))(synth.er(100, 3.0, seed=1)))
+    for bad in (dict(cluster_ctas=0), dict(cluster_ctas=17)):
+        with pytest.raises(abfs.AbfsError) as ei:
+            abfs.run(G, 0, params=_params(**bad))
+        assert ei.value.status == 1
+    G.destroy()
+
+
 def test_hybrid_parameter_rules():
     G = abfs.graph_create(*(lambda g: (g.colptr, g.rowidx))(synth.er(100, 3.0, seed=1)))
     for bad in (dict(mode=PLAIN, bottom_up_alpha=14),
@@ -429,8 +480,9 @@ def test_batch_512_graphs_as_benchmarked():
 def test_grid_4096():
     g = synth.grid_4096()
     G = abfs.graph_create(g.colptr, g.rowidx, directed=False)
-    for mode in (SUB, PLAIN):
-        level, parent, st = abfs.run(G, 0, params=_params(mode=mode), stats=True)
+    for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, cluster_ctas=1),
+               dict(mode=SUB, cluster_ctas=16)):
+        level, parent, st = abfs.run(G, 0, params=_params(**kw), stats=True)
         assert st["status"] == 0 and st["levels"] == 8191
         lev = level.cpu().numpy()
         par = parent.cpu().numpy()
@@ -446,7 +498,7 @@ def test_grid_4096():
 def test_rgg_2_22():
     g = synth.rgg_2_22()
     G = abfs.graph_create(g.colptr, g.rowidx, directed=True)
-    for mode in (SUB, PLAIN):
-        level, parent = abfs.run(G, 0, params=_params(mode=mode))
-        _check(g, 0, level, parent, f"rgg22 mode{mode}")
+    for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, cluster_ctas=1)):
+        level, parent = abfs.run(G, 0, params=_params(**kw))
+        _check(g, 0, level, parent, f"rgg22 {kw}")
     G.destroy()
