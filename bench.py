@@ -565,6 +565,7 @@ def main():
     ap.add_argument("--shrink", type=float, default=0.0)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="library defaults instead of abfs_tune")
     ap.add_argument("--no-batch-serve", action="store_true",
                     help="default workload: skip the 576-query batch and the serving run")
     args = ap.parse_args()
@@ -593,7 +594,13 @@ def main():
     g, srcs, (wname, wdesc) = make_workload(args.workload)
     G = abfs.graph_create(g.colptr, g.rowidx, directed=g.directed)
     mode = abfs.MODE_PLAIN if args.mode == "plain" else abfs.MODE_SUBMATRIX
-    params = abfs.default_params(mode=mode)
+    # launch parameters for this graph from the library's autotuner (granule,
+    # narrow bounds, cluster size, shrink threshold), on a few of the sources
+    tune_srcs = srcs[:4]
+    if args.no_tune:
+        params, tune_ms = abfs.default_params(mode=mode), None
+    else:
+        params, tune_ms = abfs.tune(G, tune_srcs, mode)
     if args.shrink > 0:
         params.shrink_theta = args.shrink
         params.shrink_max = 1
@@ -678,7 +685,10 @@ def main():
                    "step": f"{nsrc} single-source BFS via abfs_run",
                    "l2": f"inputs larger than L2: rowidx {g.nnz * 4 / 1e6:.0f} MB",
                    "parallelism": f"replicas x{ws}", "edges": "m_c = nnz_c/2" if not g.directed
-                   else "m_c = nnz_c"},
+                   else "m_c = nnz_c",
+                   "params": params.as_dict(),
+                   "params_from": "defaults" if args.no_tune else
+                   f"abfs_tune on {len(tune_srcs)} of the sources ({tune_ms:.3f} ms per search)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
                      "traffic": _profiled_traffic(wname),
@@ -715,8 +725,10 @@ def main():
                    "steps": e2e_steps, "api": "abfs_run_host into pinned host buffers"}
 
     if not args.no_extras and ws == 1:
-        # comparator on the same GPU: plain masked SpMSpV (multiply, then mask)
-        pp = abfs.default_params(mode=abfs.MODE_PLAIN)
+        # comparator on the same GPU: plain masked SpMSpV (multiply, then mask),
+        # tuned for itself in the same way
+        pp = abfs.default_params(mode=abfs.MODE_PLAIN) if args.no_tune else \
+            abfs.tune(G, tune_srcs, abfs.MODE_PLAIN)[0]
         for s in srcs:
             abfs.run(G, int(s), level, parent, stream, pp)
         torch.cuda.synchronize()
@@ -732,7 +744,8 @@ def main():
         cms = a.elapsed_time(b)
         cval = edges_per_step * c_steps / (cms * 1e-3) / 1e9
         line["comparator"] = {"name": "plain masked SpMSpV (same engine, multiply then mask)",
-                              "value": cval, "unit": "GTEPS", "speedup_of_ours": value / cval}
+                              "value": cval, "unit": "GTEPS", "speedup_of_ours": value / cval,
+                              "params": pp.as_dict()}
         # same GPU, same search, two variants beside the paper's method: the
         # direction-optimising hybrid (bottom-up levels; identical results) and
         # the shortest-path counts of the all-nonzero variant (abfs_run_counts)
@@ -748,7 +761,9 @@ def main():
             torch.cuda.synchronize()
             return a.elapsed_time(b) / reps
 
-        hp = abfs.default_params(bottom_up_alpha=5, bottom_up_beta=24)
+        hp = abfs.Params.from_buffer_copy(params)
+        hp.bottom_up_alpha, hp.bottom_up_beta = 5, 24
+        hp.shrink_theta, hp.shrink_max = 0.0, 0
         if not g.directed:
             hms = timed(lambda s: abfs.run(G, s, level, parent, stream, hp), c_steps)
             hval = edges_per_step / (hms * 1e-3) / 1e9

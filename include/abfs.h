@@ -113,8 +113,10 @@ typedef struct {
                                  per-level barrier live in the leading CTA's shared memory
                                  (distributed shared memory).  Results are identical. */
     uint32_t cluster_min;     /* a level of >= this many entry slots starts a cluster run
-                                 (smaller ones run on one CTA; a larger level that a
-                                 single CTA may not take starts one too) */
+                                 (smaller ones run on one CTA; a search's first level and a
+                                 level too large for one CTA may start one too).  A run
+                                 starts only while at least half of the cluster's other
+                                 CTAs are idle. */
     uint32_t cluster_max;     /* a cluster run continues while a level has <= this many
                                  frontier vertices ... */
     uint32_t cluster_edges;   /* ... and <= this many entry slots (column entries + 2 per

@@ -129,7 +129,7 @@ abfs_params default_params() {
     p.bottom_up_alpha = 0;
     p.bottom_up_beta = 24;
     p.cluster_ctas = 8;
-    p.cluster_min = 0;
+    p.cluster_min = 2048;
     p.cluster_max = 16384;
     p.cluster_edges = 1u << 15;
     return p;

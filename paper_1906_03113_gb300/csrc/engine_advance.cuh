@@ -203,7 +203,8 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
             trace_put(I, ctl, nkind, nk, alone, nkind == kPhPlainMask ? ni : units, nf, ne);
         // a small level runs on this CTA and the idle CTAs of its cluster
         if (P.cluster > 1 && P.narrow_loop && (nkind == kPhLevel || nkind == kPhPlainMult) &&
-            (ne >= P.cluster_min || !alone) && nf <= P.cluster_max && ne <= P.cluster_edges) {
+            (nk == 0 || ne >= P.cluster_min || !alone) && nf <= P.cluster_max &&
+            ne <= P.cluster_edges) {
             if (threadIdx.x < 32) {
                 const uint32_t mem = cluster_try_lead(sm, sm.cmd.q, nk);
                 if (threadIdx.x == 0) sm.cr_join = mem;

@@ -69,7 +69,9 @@ __device__ ABFS_NOINLINE uint32_t cluster_try_lead(Smem& sm, uint32_t q, uint32_
     const uint32_t C = cluster_size(), me = cluster_rank();
     const uint32_t invited = cluster_idle_peers(sm);
     uint32_t result = 0;
-    if (lane == 0 && invited) {
+    // a run with few members helps little and keeps busy CTAs waiting: at
+    // least half of the other CTAs must be idle
+    if (lane == 0 && 2u * __popc(invited) >= C - 1u && invited) {
         const uint32_t lock_a = ds_addr(&sm.cbox.lock, 0);
         if (ds_cas(lock_a, 0u, me + 1u) == 0u) {
             // run numbers are unique in the cluster (the leader's rank in the low

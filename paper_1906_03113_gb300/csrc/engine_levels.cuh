@@ -437,7 +437,8 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
             uint32_t idle = 0;
             if (sl >= P.cluster_min && sl <= P.cluster_edges && fn <= P.cluster_max)
                 idle = cluster_idle_peers(sm);
-            if (threadIdx.x == 0) sm.cr_idle = idle;
+            // as for starting a run: at least half of the other CTAs idle
+            if (threadIdx.x == 0) sm.cr_idle = 2u * __popc(idle) >= cluster_size() - 1u ? idle : 0u;
         }
         if (threadIdx.x == 0) {
             const uint32_t fn = sm.nq_cnt;
