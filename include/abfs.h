@@ -121,6 +121,12 @@ typedef struct {
                                  frontier vertices ... */
     uint32_t cluster_edges;   /* ... and <= this many entry slots (column entries + 2 per
                                  vertex) */
+    uint32_t multi_source;    /* batches (submatrix mode, no path counts): when at least
+                                 this many queries search one undirected graph, they run as
+                                 multi-source searches of up to 64 sources each -- one
+                                 64-bit mask per vertex, so a column of the union frontier
+                                 is read once per level for all its sources.  0: never.
+                                 Results are identical to single searches. */
 } abfs_params;
 
 /* Per-search counters, filled when a stats pointer is passed. */

@@ -53,6 +53,7 @@ class Params(ctypes.Structure):
         ("cluster_min", ctypes.c_uint32),
         ("cluster_max", ctypes.c_uint32),
         ("cluster_edges", ctypes.c_uint32),
+        ("multi_source", ctypes.c_uint32),
     ]
 
     def as_dict(self) -> dict:
@@ -331,7 +332,8 @@ def calibrate(words_log2: int = 22, stream=None) -> dict:
 
 
 TRACE_KINDS = {0: "level", 1: "plain_mult", 2: "plain_mask", 3: "shrink", 4: "init",
-               5: "level_scan", 6: "extract", 7: "bu_prep", 8: "bottom_up", 0xFE: "start",
+               5: "level_scan", 6: "extract", 7: "bu_prep", 8: "bottom_up", 10: "ms_level",
+               11: "ms_update", 0xFE: "start",
                0xFF: "end"}
 
 

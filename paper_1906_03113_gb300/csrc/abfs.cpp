@@ -132,6 +132,7 @@ abfs_params default_params() {
     p.cluster_min = 2048;
     p.cluster_max = 16384;
     p.cluster_edges = 1u << 15;
+    p.multi_source = 8;
     return p;
 }
 
@@ -190,7 +191,7 @@ bool same_layout(const abfs_params& a, const abfs_params& b) {
 // per-search workspace layout
 // ---------------------------------------------------------------------------
 
-Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p) {
+Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p, uint32_t ms) {
     Layout L;
     std::memset(&L, 0, sizeof(L));
     const size_t A = 256;
@@ -202,7 +203,9 @@ Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p) {
     };
     L.nwords = (n + 31) / 32;
     L.bcap = std::min<uint32_t>(n, kBlockMask);
-    L.ucap = (nnz + n) / p.unit_entries + 2;
+    // a level's frontier holds at most every vertex: nnz column entries plus
+    // kVertexSlots per vertex
+    L.ucap = (nnz + (uint64_t)kVertexSlots * n) / p.unit_entries + 2;
     L.ctl = take(sizeof(InstCtl));
     L.inst = take(sizeof(Inst));
     for (int i = 0; i < 2; ++i) {
@@ -220,7 +223,17 @@ Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p) {
         L.y = take((size_t)n * 8);
         L.touched = take((size_t)n * 4);
     }
-    if (shrink_enabled(p)) {
+    if (ms) {
+        // multi-source search: reached / frontier / next bit masks, the sources
+        // and the per-source output pointers
+        L.ms_vis = take((size_t)n * 8);
+        for (int i = 0; i < 2; ++i) L.ms_fr[i] = take((size_t)n * 8);
+        L.ms_nx = take((size_t)n * 8);
+        L.ms_src = take((size_t)ms * 4);
+        L.ms_lev = take((size_t)ms * 8);
+        L.ms_par = take((size_t)ms * 8);
+    }
+    if (shrink_enabled(p) && !ms) {
         L.ncopies = std::min(p.shrink_max, 2u);
         L.scap = nnz;
         for (uint32_t i = 0; i < L.ncopies; ++i) {
@@ -706,10 +719,12 @@ struct abfs_batch_s {
     Inst* d_insts = nullptr;
     uint32_t* d_done = nullptr;
     unsigned long long* d_beat = nullptr;
-    std::vector<size_t> ctl_off; // offset of each InstCtl in ws
+    std::vector<size_t> ctl_off; // offset of each search instance's InstCtl in ws
+    std::vector<uint32_t> qinst; // query -> the search instance that answers it
+    uint32_t ninst = 0;          // search instances (a multi-source search answers several queries)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    InstCtl* h_ctl = nullptr;    // pinned, count entries
+    InstCtl* h_ctl = nullptr;    // pinned, ninst entries
 };
 
 extern "C" int abfs_batch_destroy(abfs_batch_t b) {
@@ -747,41 +762,121 @@ int batch_create(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
     b->graphs.assign(g, g + count);
     b->count = count;
     b->p = p;
-    std::vector<Layout> L(count);
-    std::vector<size_t> base(count);
+    // search instances: the queries on one undirected graph run as multi-source
+    // searches of up to kMsMax sources when there are at least p.multi_source of
+    // them (submatrix mode, no path counts); every other query runs alone
+    struct Search {
+        uint32_t gi;                  // a query on the instance's graph
+        std::vector<uint32_t> q;      // its queries (one unless multi-source)
+    };
+    std::vector<Search> inst;
+    b->qinst.assign(count, 0);
+    {
+        std::vector<char> done(count, 0);
+        const bool group = p.multi_source >= 1 && p.mode == ABFS_MODE_SUBMATRIX && !sigma;
+        for (uint32_t i = 0; i < count; ++i) {
+            if (done[i]) continue;
+            std::vector<uint32_t> same;
+            // the parent rule of multi-source searches scans a vertex's column
+            // (= its in-neighbours) in ascending order: undirected, sorted graphs
+            if (group && !g[i]->directed && g[i]->sorted)
+                for (uint32_t j = i; j < count; ++j)
+                    if (!done[j] && g[j] == g[i]) same.push_back(j);
+            if (same.size() >= std::max<uint32_t>(p.multi_source, 2u)) {
+                for (size_t c0 = 0; c0 < same.size(); c0 += kMsMax) {
+                    Search m;
+                    m.gi = i;
+                    for (size_t c = c0; c < std::min(same.size(), c0 + kMsMax); ++c) {
+                        m.q.push_back(same[c]);
+                        done[same[c]] = 1;
+                    }
+                    inst.push_back(m);
+                }
+            } else {
+                Search one;
+                one.gi = i;
+                one.q.push_back(i);
+                done[i] = 1;
+                inst.push_back(one);
+            }
+        }
+    }
+    const uint32_t ninst = (uint32_t)inst.size();
+    b->ninst = ninst;
+    std::vector<Layout> L(ninst);
+    std::vector<size_t> base(ninst);
     size_t total = 0;
     uint32_t max_n = 0;
-    for (uint32_t i = 0; i < count; ++i) {
-        L[i] = layout_for(g[i]->n, g[i]->nnz, p);
-        base[i] = total;
-        total = align_up(total + L[i].total, 256);
-        max_n = std::max(max_n, g[i]->n);
+    for (uint32_t t = 0; t < ninst; ++t) {
+        const abfs_graph_s* gt = g[inst[t].gi];
+        const uint32_t ms = inst[t].q.size() > 1 ? (uint32_t)inst[t].q.size() : 0u;
+        L[t] = layout_for(gt->n, gt->nnz, p, ms);
+        base[t] = total;
+        total = align_up(total + L[t].total, 256);
+        max_n = std::max(max_n, gt->n);
     }
     rc = dev_alloc((void**)&b->ws, total);
-    if (!rc) rc = dev_alloc((void**)&b->d_insts, sizeof(Inst) * count);
+    if (!rc) rc = dev_alloc((void**)&b->d_insts, sizeof(Inst) * ninst);
     if (!rc) rc = dev_alloc((void**)&b->d_done, 64);
     if (!rc) rc = dev_alloc((void**)&b->d_beat, 64);
     if (rc) {
         abfs_batch_destroy(b);
         return rc;
     }
-    if (cudaMallocHost((void**)&b->h_ctl, sizeof(InstCtl) * count) != cudaSuccess) {
+    if (cudaMallocHost((void**)&b->h_ctl, sizeof(InstCtl) * ninst) != cudaSuccess) {
         cudaGetLastError();
         abfs_batch_destroy(b);
         return ABFS_ERR_OOM;
     }
-    std::vector<Inst> hI(count);
-    b->ctl_off.resize(count);
-    for (uint32_t i = 0; i < count; ++i) {
-        hI[i] = make_inst(g[i], b->ws + base[i], L[i], sources[i], level[i], parent[i]);
-        if (sigma) {
-            // path counts: every multiplied entry contributes, so the search stays top-down
-            hI[i].sigma = reinterpret_cast<unsigned long long*>(sigma[i]);
-            hI[i].bu_ok = 0;
+    std::vector<Inst> hI(ninst);
+    b->ctl_off.resize(ninst);
+    for (uint32_t t = 0; t < ninst; ++t) {
+        const Search& m = inst[t];
+        const abfs_graph_s* gt = g[m.gi];
+        char* wb = b->ws + base[t];
+        for (uint32_t q : m.q) b->qinst[q] = t;
+        if (m.q.size() == 1) {
+            const uint32_t q = m.q[0];
+            hI[t] = make_inst(gt, wb, L[t], sources[q], level[q], parent[q]);
+            if (sigma) {
+                // path counts: every multiplied entry contributes, so the search stays top-down
+                hI[t].sigma = reinterpret_cast<unsigned long long*>(sigma[q]);
+                hI[t].bu_ok = 0;
+            }
+        } else {
+            // multi-source: the sources and the outputs' pointers go to the workspace
+            const uint32_t ms = (uint32_t)m.q.size();
+            std::vector<uint32_t> src(ms);
+            std::vector<int32_t*> lv(ms), pv(ms);
+            for (uint32_t s2 = 0; s2 < ms; ++s2) {
+                src[s2] = sources[m.q[s2]];
+                lv[s2] = level[m.q[s2]];
+                pv[s2] = parent[m.q[s2]];
+            }
+            cudaError_t ce = cudaMemcpy(wb + L[t].ms_src, src.data(), 4 * ms, cudaMemcpyHostToDevice);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpy(wb + L[t].ms_lev, lv.data(), 8 * ms, cudaMemcpyHostToDevice);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpy(wb + L[t].ms_par, pv.data(), 8 * ms, cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) {
+                abfs_batch_destroy(b);
+                return cuda_fail(ce);
+            }
+            hI[t] = make_inst(gt, wb, L[t], src[0], nullptr, nullptr);
+            hI[t].bu_ok = 0;
+            hI[t].ms = ms;
+            hI[t].ms_sorted = gt->sorted ? 1u : 0u;
+            hI[t].ms_vis = reinterpret_cast<unsigned long long*>(wb + L[t].ms_vis);
+            for (int i2 = 0; i2 < 2; ++i2)
+                hI[t].ms_fr[i2] = reinterpret_cast<unsigned long long*>(wb + L[t].ms_fr[i2]);
+            hI[t].ms_nx = reinterpret_cast<unsigned long long*>(wb + L[t].ms_nx);
+            hI[t].ms_src = reinterpret_cast<const uint32_t*>(wb + L[t].ms_src);
+            hI[t].ms_level = reinterpret_cast<int32_t* const*>(wb + L[t].ms_lev);
+            hI[t].ms_parent = reinterpret_cast<int32_t* const*>(wb + L[t].ms_par);
         }
-        b->ctl_off[i] = base[i] + L[i].ctl;
+        b->ctl_off[t] = base[t] + L[t].ctl;
     }
-    cudaError_t e = cudaMemcpy(b->d_insts, hI.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(b->d_insts, hI.data(), sizeof(Inst) * ninst, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         abfs_batch_destroy(b);
         return cuda_fail(e);
@@ -795,7 +890,7 @@ int batch_create(const abfs_graph_t* g, const uint32_t* sources, uint32_t count,
     }
     EngineArgs a;
     a.insts = b->d_insts;
-    a.ninst = count;
+    a.ninst = ninst;
     a.done_count = b->d_done;
     a.heartbeat = b->d_beat;
     a.prof = nullptr;
@@ -850,13 +945,13 @@ extern "C" int abfs_batch_launch(abfs_batch_t b, abfs_stream_t stream) {
 extern "C" int abfs_batch_status(abfs_batch_t b, abfs_stream_t stream, int32_t* status) {
     if (!b || !status) return ABFS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    for (uint32_t i = 0; i < b->count; ++i)
+    for (uint32_t i = 0; i < b->ninst; ++i)
         CK(cudaMemcpyAsync(b->h_ctl + i, b->ws + b->ctl_off[i], sizeof(InstCtl),
                            cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     int worst = ABFS_OK;
     for (uint32_t i = 0; i < b->count; ++i) {
-        const InstCtl& c = b->h_ctl[i];
+        const InstCtl& c = b->h_ctl[b->qinst[i]];
         status[i] = (c.status == kDone) ? ABFS_OK : (c.err ? (int)c.err : ABFS_ERR_DEVICE);
         if (status[i] && !worst) worst = status[i];
     }

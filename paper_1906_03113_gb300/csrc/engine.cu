@@ -67,6 +67,28 @@ __global__ void init_fill_kernel(const Inst* insts, uint32_t ninst, uint32_t mod
     const Inst& I = insts[blockIdx.y];
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I.ms) {
+        // multi-source search: every source's outputs, the bit masks, the control block
+        for (uint32_t s = 0; s < I.ms; ++s) {
+            int32_t* lv = I.ms_level[s];
+            int32_t* pv = I.ms_parent[s];
+            for (uint32_t v = t0; v < I.n; v += stride) {
+                lv[v] = -1;
+                pv[v] = -1;
+            }
+        }
+        for (uint32_t v = t0; v < I.n; v += stride) {
+            I.ms_vis[v] = 0ull;
+            I.ms_fr[0][v] = 0ull;
+            I.ms_fr[1][v] = 0ull;
+            I.ms_nx[v] = 0ull;
+        }
+        if (blockIdx.x == 0) {
+            uint32_t* c = reinterpret_cast<uint32_t*>(I.ctl);
+            for (uint32_t w = threadIdx.x; w < sizeof(InstCtl) / 4; w += blockDim.x) c[w] = 0u;
+        }
+        return;
+    }
     for (uint32_t v = t0; v < I.n; v += stride) {
         I.level[v] = -1;
         I.parent[v] = kUnset;
@@ -103,6 +125,40 @@ __global__ void init_source_kernel(EngineArgs a) {
     const Inst& I = a.insts[q];
     const EngineParams& P = a.p;
     InstCtl* ctl = I.ctl;
+    unsigned long long w0 = 0;  // entry slots of the frontier of level 0
+    if (I.ms) {
+        // multi-source search: x_1 = e_src for every source bit; the frontier of
+        // level 0 is the distinct sources, one block
+        uint32_t nv = 0;
+        unsigned long long w = 0;  // entry slots so far
+        for (uint32_t b = 0; b < I.ms; ++b) {
+            const uint32_t v = I.ms_src[b];
+            I.ms_level[b][v] = 0;
+            I.ms_parent[b][v] = (int32_t)v;
+            const unsigned long long bit = 1ull << b;
+            if (I.ms_fr[0][v] == 0ull) {
+                // first source at v: v joins the frontier list
+                const uint32_t len = I.colptr[v + 1] - I.colptr[v];
+                I.fq[0][nv] = v;
+                I.fbeg[0][nv] = I.colptr[v];
+                I.fpre[0][nv] = (uint32_t)w;
+                const unsigned long long w1 = w + len + kVertexSlots;
+                for (unsigned long long x = (w + P.unit - 1) / P.unit * P.unit; x < w1; x += P.unit)
+                    I.ustart[0][x / P.unit] = make_uint2(0, nv);
+                w = w1;
+                ++nv;
+            }
+            I.ms_fr[0][v] |= bit;
+            I.ms_vis[v] |= bit;
+        }
+        I.blk[0][0].vb = 0;
+        I.blk[0][0].nv = nv;
+        I.blk[0][0].eb = 0;
+        ctl->bctr[0] = (w << kBlockBits) | 1ull;
+        ctl->fcnt[0] = nv;
+        ctl->reached = nv;
+        w0 = w;
+    } else {
     const uint32_t s = I.src;
     I.level[s] = 0;
     I.parent[s] = s;
@@ -121,6 +177,8 @@ __global__ void init_source_kernel(EngineArgs a) {
     ctl->bctr[0] = ((unsigned long long)w << kBlockBits) | 1ull;
     ctl->fcnt[0] = 1;
     ctl->reached = 1;
+    w0 = w;
+    }
     ctl->mat_cur = 0;
     ctl->mat_prev = 0;
     ctl->mat_switch = 0;
@@ -138,7 +196,7 @@ __global__ void init_source_kernel(EngineArgs a) {
     if (I.trace && I.trace_cap) {
         const uint64_t now = globaltimer();
         I.trace[0] = make_uint4((uint32_t)now, (uint32_t)(now >> 32), (0xFEu << 24), 0u);
-        I.trace[1] = make_uint4(0u, 1u, w, 0u);
+        I.trace[1] = make_uint4(0u, ctl->fcnt[0], (uint32_t)w0, 0u);
         ctl->trace_n = 1;
     }
 }

@@ -38,8 +38,12 @@ __device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const Eng
         nk = 0;
     } else if (kind == kPhStart) {
         // the frontier of level 0 (the source) was set up before the launch
-        nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
+        nkind = (MODE == kModePlain) ? kPhPlainMult : (I.ms ? kPhMsLevel : kPhLevel);
         nk = 0;
+    } else if (kind == kPhMsLevel) {
+        // the new bits of a multi-source level become levels, parents, frontier
+        nkind = kPhMsUpdate;
+        nk = k;
     } else if (kind == kPhLevelScan) {
         // the new vertices of a level claimed by reductions are read off the bitmaps
         nkind = kPhExtract;
@@ -85,8 +89,8 @@ __device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const Eng
             st_relaxed(&ctl->shrinks, shrinks);
         }
         if (!finish) {
-            const bool do_shrink =
-                MODE == kModeSub && kind != kPhShrink && shrink_due(P, reached, I.n, shrinks);
+            const bool do_shrink = MODE == kModeSub && !I.ms && kind != kPhShrink &&
+                                   shrink_due(P, reached, I.n, shrinks);
             if (do_shrink) {
                 // alternate copies so the frontier of level k+1 keeps its matrix
                 const uint32_t cur = ld_relaxed(&ctl->mat_cur);
@@ -95,7 +99,7 @@ __device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const Eng
                 ni = (cur == 1) ? 2u : 1u;
                 st_relaxed(&ctl->shrink_out, 0u);
             } else {
-                nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
+                nkind = (MODE == kModePlain) ? kPhPlainMult : (I.ms ? kPhMsLevel : kPhLevel);
                 nk = k + 1;
                 if (MODE == kModeSub && P.bu_alpha && I.bu_ok && kind != kPhShrink) {
                     // hybrid direction choice from the frontier's edges m_f and the
@@ -174,7 +178,8 @@ __device__ void advance(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem
         } else if (nkind == kPhPlainMask) {
             units = (ni + P.tile - 1) / P.tile;
             alone = ni <= P.narrow_max;
-        } else if (nkind == kPhExtract || nkind == kPhBuPrep || nkind == kPhBottomUp) {
+        } else if (nkind == kPhExtract || nkind == kPhBuPrep || nkind == kPhBottomUp ||
+                   nkind == kPhMsUpdate) {
             // runs of 8-word chunks, about two units per CTA (ni = chunks per unit)
             const uint32_t chunks = (I.nwords + kChunkWords - 1) / kChunkWords;
             const uint32_t two = 2u * gridDim.x;

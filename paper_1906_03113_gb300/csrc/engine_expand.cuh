@@ -17,10 +17,15 @@ enum ClaimVar : int {
     kVarNarrow = 1,  // the same inside a resident narrow run (plain frontier list)
     kVarScan = 2,    // reductions only: atomicMin and the bit in the write bitmap without
                      // return; an extraction phase collects the new vertices afterwards
+    kVarMs = 3,      // multi-source search: the next-bit mask of row r gets the frontier
+                     // bits of column j that r has not reached (a 64-bit reduction); an
+                     // update phase turns them into levels, parents and the next frontier
 };
 
 // Groups of 32 entries each thread keeps in flight, per claim variant.
-__host__ __device__ constexpr int ilp_of(int var) { return var == kVarScan ? kIlpScan : kIlp; }
+__host__ __device__ constexpr int ilp_of(int var) {
+    return (var == kVarScan || var == kVarMs) ? kIlpScan : kIlp;
+}
 
 // Entries (r[u] in column j[u]; r[u] == kUnset: none) at level k.  Each stage issues
 // kIlp independent memory operations before consuming any.  Submatrix mode
@@ -33,6 +38,28 @@ __device__ __forceinline__ void process_group(const Inst& I, InstCtl* ctl, const
                                               uint32_t& wc) {
     constexpr int L = ilp_of(VAR);
     const uint32_t p = k & 1;
+    if (VAR == kVarMs) {
+        // x_{k+1}(r) gets, for every source s, the product of frontier column j
+        // with row r masked by r's reached set: one bit per source.  fr and vis
+        // change only between phases (plain loads after the unit's acquire).
+        const unsigned long long* fr = I.ms_fr[p];
+        unsigned long long fm[L], vv[L];
+#pragma unroll
+        for (int u = 0; u < L; ++u) {
+            fm[u] = r[u] != kUnset ? fr[j[u]] : 0ull;
+            vv[u] = r[u] != kUnset ? I.ms_vis[r[u]] : ~0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < L; ++u) {
+            const unsigned long long nb = fm[u] & ~vv[u];
+            if (nb) {
+                ++t.unmasked;
+                ++t.claims;
+                atomicOr(I.ms_nx + r[u], nb);
+            }
+        }
+        return;
+    }
     if (MODE == kModeSub) {
         const uint32_t* test_bm = I.bm[p];
         uint32_t* write_bm = I.bm[p ^ 1];
@@ -260,7 +287,7 @@ __device__ __forceinline__ void expand_core(const Inst& I, InstCtl* ctl, const E
         const long long xp1 = sm.prof_on ? clock64() : 0ll;
         xproc += xp1 - xp0;
 #endif
-        if (VAR == kVarScan) {
+        if (VAR == kVarScan || VAR == kVarMs) {
             // nothing staged
         } else if (VAR == kVarNarrow) {
             if (wc > (uint32_t)kWarpFlushAt) {
@@ -421,7 +448,7 @@ __device__ ABFS_NOINLINE void unit_level(const Inst& I, InstCtl* ctl, const Engi
                 // set of the next level's test (once), and starts a run of slots
                 atomicOr(&sm.sbits[(st - lo) >> 5], 1u << ((st - lo) & 31));
                 const uint32_t v = sm.v[s];
-                if (MODE == kModeSub) atomicOr(I.bm[p ^ 1] + (v >> 5), 1u << (v & 31));
+                if (MODE == kModeSub && VAR != kVarMs) atomicOr(I.bm[p ^ 1] + (v >> 5), 1u << (v & 31));
                 nnz_local += (mat == 0) ? len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
             }
         }
@@ -442,7 +469,7 @@ __device__ ABFS_NOINLINE void unit_level(const Inst& I, InstCtl* ctl, const Engi
     if ((threadIdx.x & 31) == 0 && nnz_local) atomicAdd(&sm.st_nnz, (unsigned long long)nnz_local);
     tally_flush(sm, t);
     const long long pt3 = prof_now(sm);
-    if (MODE == kModeSub && VAR != kVarScan) cta_flush(sm, I, ctl, P, p ^ 1, mat_next);
+    if (MODE == kModeSub && VAR != kVarScan && VAR != kVarMs) cta_flush(sm, I, ctl, P, p ^ 1, mat_next);
     prof_add(sm, kProfFlush, pt3);
 }
 

@@ -33,6 +33,10 @@ __device__ void run_unit(const Inst& I, InstCtl* ctl, const EngineParams& P, Sme
         unit_bottom_up(I, ctl, P, sm, k, unit, nitems);
     } else if (MODE == kModeSub && kind == kPhLevelScan) {
         unit_level<MODE, kVarScan>(I, ctl, P, sm, k, unit, nitems);
+    } else if (MODE == kModeSub && kind == kPhMsLevel) {
+        unit_level<MODE, kVarMs>(I, ctl, P, sm, k, unit, nitems);
+    } else if (MODE == kModeSub && kind == kPhMsUpdate) {
+        unit_ms_update(I, ctl, P, sm, k, unit, nitems);
     } else {
         unit_level<MODE, kVarWide>(I, ctl, P, sm, k, unit, nitems);
     }

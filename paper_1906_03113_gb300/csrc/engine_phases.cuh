@@ -132,6 +132,118 @@ __device__ ABFS_NOINLINE void unit_bottom_up(const Inst& I, InstCtl* ctl, const 
     cta_flush(sm, I, ctl, P, (k & 1) ^ 1, mat_next);
 }
 
+// ---------------------------------------------------------------------------
+// multi-source searches: the update phase of a level
+// ---------------------------------------------------------------------------
+//
+// After the expand phase of level k, ms_nx[v] holds the sources (bits) that
+// reach v first at level k+1.  For each such source s, v's parent is the least
+// frontier vertex j of level k, for s, that has v in its column; on an
+// undirected graph that is the least j in v's own column with bit s in
+// ms_fr[k&1][j], and with the column ascending the first such entry.  A lane
+// scans its vertex's column itself for the first entries, four at a time;
+// longer scans run on the whole warp, 32 entries at a time, where each lane
+// keeps the bits no lower lane has (a prefix OR across the warp).
+
+// Outputs of vertex v for the sources in `bits`: level k+1, parent j.
+__device__ __forceinline__ void ms_write(const Inst& I, uint32_t k, uint32_t v, uint32_t j,
+                                         unsigned long long bits) {
+    while (bits) {
+        const uint32_t s = (uint32_t)(__ffsll((long long)bits) - 1);
+        bits &= bits - 1;
+        I.ms_level[s][v] = (int32_t)(k + 1);
+        I.ms_parent[s][v] = (int32_t)j;
+    }
+}
+
+// Inclusive prefix OR of a 64-bit value across the warp's lanes.
+__device__ __forceinline__ unsigned long long warp_prefix_or(unsigned long long x) {
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= (uint32_t)d) x |= y;
+    }
+    return x;
+}
+
+// Unit u of the update of level k: chunks [u*per, (u+1)*per) of 8 x 32 vertices.
+__device__ ABFS_NOINLINE void unit_ms_update(const Inst& I, InstCtl* ctl, const EngineParams& P,
+                                             Smem& sm, uint32_t k, uint32_t u, uint32_t per) {
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t p = k & 1, pn = p ^ 1;
+    const unsigned long long* fr = I.ms_fr[p];
+    const uint32_t chunks = (I.nwords + kChunkWords - 1) / kChunkWords;
+    const uint32_t c1 = min(chunks, (u + 1) * per);
+    uint32_t wc = sm.wcnt[warp];
+    Tally t;
+    for (uint32_t c = u * per + warp; c < c1; c += kWarps) {
+        for (uint32_t q = 0; q < kChunkWords; ++q) {
+            const uint32_t v = (c * kChunkWords + q) * 32 + lane;
+            unsigned long long nb = 0;
+            uint32_t e = 0, end = 0;
+            if (v < I.n) {
+                nb = ld_l2(I.ms_nx + v);
+                // every vertex gets its bits of the next frontier (0: none)
+                I.ms_fr[pn][v] = nb;
+                if (nb) {
+                    I.ms_nx[v] = 0ull;
+                    I.ms_vis[v] = ld_l2(I.ms_vis + v) | nb;
+                    e = ld_ro(I.colptr + v);
+                    end = ld_ro(I.colptr + v + 1);
+                }
+            }
+            unsigned long long rem = nb;
+            for (uint32_t b = 0; b < kBuLaneBatches && rem && e < end; ++b) {
+                uint32_t jj[4];
+                unsigned long long fm[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) jj[x] = e + x < end ? ld_ro(I.rowidx + e + x) : kUnset;
+#pragma unroll
+                for (int x = 0; x < 4; ++x) fm[x] = jj[x] != kUnset ? ld_l2(fr + jj[x]) : 0ull;
+                t.read += min(4u, end - e);
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const unsigned long long hit = fm[x] & rem;
+                    if (hit) {
+                        ms_write(I, k, v, jj[x], hit);
+                        rem &= ~hit;
+                    }
+                }
+                e += 4;
+            }
+            bool defer = rem != 0 && e < end;
+            uint32_t dm;
+            while ((dm = __ballot_sync(0xFFFFFFFFu, defer)) != 0u) {
+                const uint32_t ldr = __ffs(dm) - 1;
+                const uint32_t lv = __shfl_sync(0xFFFFFFFFu, v, ldr);
+                const uint32_t le = __shfl_sync(0xFFFFFFFFu, e, ldr);
+                const uint32_t lend = __shfl_sync(0xFFFFFFFFu, end, ldr);
+                unsigned long long lrem = __shfl_sync(0xFFFFFFFFu, rem, ldr);
+                for (uint32_t x = le; x < lend && lrem; x += 32) {
+                    const uint32_t idx = x + lane;
+                    const uint32_t j = idx < lend ? ld_ro(I.rowidx + idx) : kUnset;
+                    const unsigned long long h = j != kUnset ? (ld_l2(fr + j) & lrem) : 0ull;
+                    const unsigned long long incl = warp_prefix_or(h);
+                    // the bits this lane's entry is the first (least) to hold
+                    const unsigned long long prev = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+                    const unsigned long long first = lane ? (h & ~prev) : h;
+                    if (first) ms_write(I, k, lv, j, first);
+                    if (lane == 0) t.read += min(32u, lend - x);
+                    lrem &= ~__shfl_sync(0xFFFFFFFFu, incl, 31);
+                }
+                if (lane == ldr) defer = false;
+            }
+            stage_warp(nb != 0ull, v, sm, wc);
+            if (wc > (uint32_t)(kWarpBuf - 32)) warp_flush(sm, I, ctl, P, pn, 0u, wc);
+        }
+    }
+    if (lane == 0) sm.wcnt[warp] = wc;
+    __syncwarp();
+    tally_flush(sm, t);
+    cta_flush(sm, I, ctl, P, pn, 0u);
+}
+
 // Shrink: compacts the unvisited columns among vertices
 // [u*shrink_tile, (u+1)*shrink_tile) to their unvisited rows (A_k = S_k A S_k
 // restricted to the columns still to be multiplied).  `vis` holds the

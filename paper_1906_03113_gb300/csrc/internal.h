@@ -77,7 +77,12 @@ enum PhaseKind : uint32_t {
     kPhBuPrep = 7,     // hybrid: the frontier bitmap of a bottom-up level that follows a top-down one
     kPhBottomUp = 8,   // hybrid: unvisited vertices scan their sorted columns for a frontier entry
     kPhStart = 9,      // one empty unit: its CTA advances into level 0 (a resident run if small)
+    kPhMsLevel = 10,   // multi-source search: expand the union frontier into the next-bit masks
+    kPhMsUpdate = 11,  // multi-source search: new bits -> levels, parents, next union frontier
 };
+
+// Largest number of sources one multi-source search carries (one bit each).
+constexpr uint32_t kMsMax = 64;
 
 enum InstStatus : uint32_t { kIdle = 0, kRunning = 1, kDone = 2, kFailed = 3 };
 
@@ -159,6 +164,16 @@ struct Inst {
     uint32_t slot;           // serving: slot index
     unsigned long long ticket;       // serving: request ticket
     unsigned long long* notify;      // serving: host-mapped word that receives ticket<<8 | status
+    // multi-source search (ms > 0): ms sources, one bit of a 64-bit mask each;
+    // level/parent/src above are unused, each source has its own outputs
+    uint32_t ms;
+    uint32_t ms_sorted;               // columns ascend: a parent scan may stop at the first hit
+    unsigned long long* ms_vis;       // vertices reached, per source bit (levels <= k)
+    unsigned long long* ms_fr[2];     // frontier bits, by level parity
+    unsigned long long* ms_nx;        // bits newly reached at the current level
+    const uint32_t* ms_src;           // the sources (ms of them)
+    int32_t* const* ms_level;         // per source: level output (n int32)
+    int32_t* const* ms_parent;        // per source: parent output (n int32)
 };
 
 struct EngineParams {
@@ -230,6 +245,7 @@ enum ProfSlot : int {
 struct Layout {
     size_t bm[2], fbm[2], fq[2], fbeg[2], fpre[2], blk[2], ustart[2], y, touched, sbeg[2], slen[2],
         srows[2], ctl, inst;
+    size_t ms_vis, ms_fr[2], ms_nx, ms_src, ms_lev, ms_par;  // multi-source searches only
     size_t total;
     uint32_t nwords, bcap, ncopies;
     unsigned long long ucap, scap;
@@ -240,7 +256,7 @@ abfs_params default_params();
 bool shrink_enabled(const abfs_params& p);
 int check_params(const abfs_params& p);
 EngineParams engine_params(const abfs_params& p);
-Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p);
+Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p, uint32_t ms = 0);
 Inst make_inst_raw(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, char* base,
                    const Layout& L, uint32_t src, int32_t* level, int32_t* parent);
 int grid_for(int sms, const abfs_params& p);
