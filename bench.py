@@ -61,23 +61,25 @@ def _engine_sha256() -> str:
 
 
 def _profiled_traffic(workload: str):
-    """DRAM bytes per engine launch from the committed ncu summary of this
-    workload, or None when the engine source changed since the capture."""
+    """(DRAM bytes per engine launch, ncu duration of that launch in us) from
+    the committed ncu summary of this workload, or (None, None) when the
+    engine source changed since the capture."""
     path = os.path.join(ROOT, "profiles", f"engine_kernel_{workload}.md")
     if not os.path.exists(path):
-        return None
+        return None, None
     fields = {}
     with open(path) as fh:
         for ln in fh:
             m = ln.strip().split(":", 1)
-            if len(m) == 2 and m[0] in ("traffic_bytes_per_launch", "engine_source_sha256"):
+            if len(m) == 2 and m[0] in ("traffic_bytes_per_launch", "engine_source_sha256",
+                                        "ncu_duration_us"):
                 fields[m[0]] = m[1].strip()
     if fields.get("engine_source_sha256") != _engine_sha256():
-        return None
+        return None, None
     try:
-        return int(fields["traffic_bytes_per_launch"])
+        return int(fields["traffic_bytes_per_launch"]), float(fields.get("ncu_duration_us", "nan"))
     except (KeyError, ValueError):
-        return None
+        return None, None
 
 
 def job_rate(units: float, ms: float, dist=None, device="cpu"):
@@ -675,6 +677,8 @@ def main():
     cal = abfs.calibrate(22)
     l2_bound_s = float(nnz_c.mean()) / (cal["load_gops"] * 1e9) + float(e_adj.mean()) / (
         cal["red_gops"] * 1e9)
+    traffic, ncu_us = _profiled_traffic(wname)
+    dram_gbs = traffic / (ncu_us * 1e-6) / 1e9 if traffic and ncu_us and ncu_us == ncu_us else None
     line = {
         "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
@@ -691,7 +695,11 @@ def main():
                    f"abfs_tune on {len(tune_srcs)} of the sources ({tune_ms:.3f} ms per search)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": _profiled_traffic(wname),
+                     "traffic": traffic,
+                     "dram_gbs": dram_gbs,
+                     "dram_frac": None if dram_gbs is None else dram_gbs / hbm,
+                     "dram_from": "ncu dram__bytes of one engine launch / its ncu duration "
+                                  "(profiles/), null if the engine changed since",
                      "kernel": "engine_kernel<0> (one launch per BFS, with 3 small init kernels)",
                      "bytes_per_bfs": float(b_alg.mean()),
                      "bytes_formula": "4*E_adj + 24*n_c",

@@ -77,7 +77,7 @@ typedef struct {
     uint32_t mode;            /* ABFS_MODE_SUBMATRIX or ABFS_MODE_PLAIN */
     uint32_t tile;            /* frontier vertices staged per step, 32..1024, multiple of 32 */
     uint32_t unit_entries;    /* granule of work units in entry slots: a power of two,
-                                 256..32768; a level's units are 1..32768/unit_entries granules,
+                                 256..65536; a level's units are 1..65536/unit_entries granules,
                                  chosen per level for about two units per CTA of the grid */
     uint32_t narrow_max;      /* frontiers of <= this many vertices ... */
     uint32_t narrow_edges;    /* ... and <= this many column entries run on one CTA */

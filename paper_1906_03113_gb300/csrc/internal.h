@@ -49,7 +49,7 @@ constexpr int kWarpBuf = 64 * kIlp < 256 ? 256 : 64 * kIlp;
 constexpr int kWarpFlushAt = kWarpBuf - 32 * kIlp;
 // Largest work unit (entry slots) and the per-unit start bitmap it needs.
 #ifndef ABFS_UNIT_MAX
-#define ABFS_UNIT_MAX 32768
+#define ABFS_UNIT_MAX 65536
 #endif
 constexpr uint32_t kUnitMax = ABFS_UNIT_MAX;
 static_assert((kUnitMax & (kUnitMax - 1)) == 0 && kUnitMax >= 1024, "unit size");
