@@ -83,16 +83,18 @@ def test_parameter_validation(lib):
         return lib.abfs_check_params(ctypes.byref(abfs.default_params(**kw)))
 
     ok, bad = 0, binding.ERR_INVALID_ARG
-    for kw in (dict(tile=32), dict(tile=1024), dict(unit_entries=256), dict(unit_entries=32768),
+    for kw in (dict(tile=32), dict(tile=1024), dict(unit_entries=256), dict(unit_entries=65536),
                dict(mode=abfs.MODE_PLAIN), dict(ctas_per_sm=1), dict(shrink_theta=0.5, shrink_max=2),
                dict(narrow_resident=0), dict(claim_scan=0), dict(claim_scan=1),
                dict(narrow_max=0, narrow_edges=0), dict(bottom_up_alpha=5, bottom_up_beta=24),
-               dict(bottom_up_alpha=0xFFFFFFFF, bottom_up_beta=0)):
+               dict(bottom_up_alpha=0xFFFFFFFF, bottom_up_beta=0), dict(cluster_ctas=1),
+               dict(cluster_ctas=16), dict(multi_source=0), dict(multi_source=64)):
         assert check(**kw) == ok, kw
     for kw in (dict(tile=16), dict(tile=1056), dict(tile=100), dict(unit_entries=128),
-               dict(unit_entries=768), dict(unit_entries=65536), dict(mode=2), dict(ctas_per_sm=0),
+               dict(unit_entries=768), dict(unit_entries=131072), dict(mode=2), dict(ctas_per_sm=0),
                dict(ctas_per_sm=9), dict(shrink_theta=-0.1), dict(shrink_theta=1.5),
-               dict(timeout_ms=0), dict(narrow_resident=2),
+               dict(timeout_ms=0), dict(narrow_resident=2), dict(cluster_ctas=0),
+               dict(cluster_ctas=17),
                # the hybrid reads the input columns: submatrix mode without shrink only
                dict(mode=abfs.MODE_PLAIN, bottom_up_alpha=5),
                dict(bottom_up_alpha=5, shrink_theta=0.5, shrink_max=1)):
