@@ -382,6 +382,14 @@ int abfs_serve_stop(abfs_server_t s, abfs_serve_report* report);
  *
  * The first call on a device looks up that array's device address (once,
  * with the device current); make that first call before any stream capture.
+ * With lazy module loading (CUDA's default) the array takes its device memory
+ * at that first lookup, so the first call on a device can fail with
+ * ABFS_ERR_CUDA when the device is out of memory: make it at start-up, before
+ * the memory is budgeted or an allocator is locked.  Later calls allocate
+ * nothing.  The scratch a search needs is about 57 bytes per vertex plus 16
+ * bytes per 1024 entry slots (column entries + 2 per vertex); graphs whose
+ * scratch exceeds the array (64 MiB - 256 bytes), e.g. beyond about 1.1
+ * million vertices at average degree 16, are rejected.
  * Every call uses the same array, which keeps the previous call's contents;
  * the call clears everything a search needs at zero.  Calls whose device work
  * overlaps (on different streams or host threads) race on the array and give

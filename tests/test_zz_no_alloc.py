@@ -7,6 +7,8 @@ twice in a row -- the array keeps the previous call's contents, so the second
 call checks that everything a search needs at zero is cleared -- and compare
 its outputs with abfs_run's.  This file is collected last on purpose.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -34,12 +36,23 @@ def _device_csc(g):
             torch.from_numpy(g.rowidx.view(np.int32)).cuda())
 
 
-@pytest.mark.parametrize("name", ["er_2_16", "rmat_16", "grid_300"])
+GRAPHS = {
+    "er_2_16": synth.er_2_16,
+    "rmat_16": lambda: synth.rmat(16, 16.0, seed=5),
+    "grid_300": lambda: synth.grid(300, 300),
+    # directed: rows that occur in no column are not pre-masked on this path
+    "rgg_2_14_directed": lambda: synth.rgg_knn(1 << 14, 4, seed=4),
+    # close to the array's limit: about 57 MB of its 64 MiB
+    "grid_1024": lambda: synth.grid(1024, 1024),
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
 def test_static_matches_run_on_two_calls_in_a_row(name):
-    g = {"er_2_16": synth.er_2_16, "rmat_16": lambda: synth.rmat(16, 16.0, seed=5),
-         "grid_300": lambda: synth.grid(300, 300)}[name]()
+    g = GRAPHS[name]()
     cp, ri = _device_csc(g)
     G = abfs.graph_create(g.colptr, g.rowidx, directed=g.directed)
+    assert G.footprint() + 256 <= 64 << 20
     deg = g.degrees()
     sources = [int(np.argmax(deg)), int(np.nonzero(deg)[0][-1])]
     for s in sources:  # two calls in a row on the same static array
@@ -67,3 +80,54 @@ def test_static_rejects_graphs_beyond_its_array():
     rc = abfs.load().abfs_run_static(cp.data_ptr(), ri.data_ptr(), 16, ri.numel(), 16,
                                      lev.data_ptr(), par.data_ptr(), None)
     assert rc == binding.ERR_INVALID_ARG
+
+
+def test_static_rejects_a_graph_just_beyond_its_array():
+    g = synth.grid(1100, 1100)
+    G = abfs.graph_create(g.colptr, g.rowidx, directed=False)
+    assert G.footprint() + 256 > 64 << 20
+    G.destroy()
+    cp, ri = _device_csc(g)
+    lev = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    par = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    assert abfs.binding.run_static(cp, ri, 0, lev, par) == binding.ERR_UNSUPPORTED
+
+
+ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def test_static_allocates_nothing_after_its_first_call():
+    """After a first call, a caller whose allocator refuses every request (a
+    hook that counts and fails) still gets exact results, the hook is never
+    called, and the device's free memory does not move."""
+    g = synth.rmat(14, 16.0, seed=3)
+    cp, ri = _device_csc(g)
+    lev = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    par = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    assert abfs.binding.run_static(cp, ri, 0, lev, par) == 0
+    torch.cuda.synchronize()
+    calls = [0]
+
+    def refuse(nbytes, ctx):
+        calls[0] += 1
+        return None
+
+    def release(p, ctx):
+        calls[0] += 1
+
+    a, f = ALLOC(refuse), FREE(release)
+    lib = abfs.load()
+    assert lib.abfs_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p),
+                                  None) == 0
+    try:
+        free0, _ = torch.cuda.mem_get_info()
+        srcs = [int(np.argmax(g.degrees())), 0]
+        for s in srcs:
+            assert abfs.binding.run_static(cp, ri, s, lev, par) == 0
+        free1, _ = torch.cuda.mem_get_info()
+    finally:
+        assert lib.abfs_set_allocator(None, None, None) == 0
+    assert calls[0] == 0 and free1 == free0
+    lo, po = oracle.bfs(g, srcs[-1])
+    assert np.array_equal(lev.cpu().numpy(), lo) and np.array_equal(par.cpu().numpy(), po)
