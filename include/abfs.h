@@ -375,7 +375,7 @@ int abfs_serve_stop(abfs_server_t s, abfs_serve_report* report);
  *
  * The caller passes device pointers: colptr[n+1] and rowidx[nnz] (CSC of A^T
  * as for abfs_graph_create, used in place, not copied or validated) and the
- * outputs level[n] and parent[n].  The scratch memory is a fixed 64 MiB
+ * outputs level[n] and parent[n].  The scratch memory is a fixed 72 MiB
  * device array inside this library (held on every GPU that loads it until the
  * process exits), enough for graphs up to about 1.1 million vertices; larger
  * inputs are rejected with ABFS_ERR_UNSUPPORTED before any device work.
@@ -386,9 +386,9 @@ int abfs_serve_stop(abfs_server_t s, abfs_serve_report* report);
  * at that first lookup, so the first call on a device can fail with
  * ABFS_ERR_CUDA when the device is out of memory: make it at start-up, before
  * the memory is budgeted or an allocator is locked.  Later calls allocate
- * nothing.  The scratch a search needs is about 57 bytes per vertex plus 16
- * bytes per 1024 entry slots (column entries + 2 per vertex); graphs whose
- * scratch exceeds the array (64 MiB - 256 bytes), e.g. beyond about 1.1
+ * nothing.  The scratch a search needs is about 65 bytes per vertex plus 16
+ * bytes per 1024 entry slots (column entries + at most 8 per vertex); graphs
+ * whose scratch exceeds the array (72 MiB - 256 bytes), e.g. beyond about 1.1
  * million vertices at average degree 16, are rejected.
  * Every call uses the same array, which keeps the previous call's contents;
  * the call clears everything a search needs at zero.  Calls whose device work
@@ -403,6 +403,9 @@ int abfs_run_static(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, 
 /*
  * Device-memory hook: alloc(bytes, ctx) returns device memory or NULL;
  * free_fn(ptr, ctx) releases it.  Both NULL restores cudaMalloc/cudaFree.
+ * Memory must be 16-byte aligned (cudaMalloc's is 256-byte aligned): a block
+ * that is not goes straight back to free_fn and the call that asked for it
+ * fails with ABFS_ERR_INVALID_ARG.
  * Applies to allocations made after the call (graphs, workspaces, plans);
  * memory must be freed by the hook that allocated it.
  */

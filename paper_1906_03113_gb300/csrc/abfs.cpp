@@ -84,7 +84,14 @@ int dev_alloc(void** p, size_t bytes) {
     }
     if (a.alloc) {
         *p = a.alloc(bytes, a.ctx);
-        return *p ? ABFS_OK : ABFS_ERR_OOM;
+        if (!*p) return ABFS_ERR_OOM;
+        // the kernels read 8- and 16-byte words from every block
+        if (reinterpret_cast<uintptr_t>(*p) & 15u) {
+            a.free(*p, a.ctx);
+            *p = nullptr;
+            return ABFS_ERR_INVALID_ARG;
+        }
+        return ABFS_OK;
     }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
@@ -204,14 +211,16 @@ Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p, uint32_t ms) {
     L.nwords = (n + 31) / 32;
     L.bcap = std::min<uint32_t>(n, kBlockMask);
     // a level's frontier holds at most every vertex: nnz column entries plus
-    // kVertexSlots per vertex
-    L.ucap = (nnz + (uint64_t)kVertexSlots * n) / p.unit_entries + 2;
+    // at most kVertexSlotsMax slots per vertex
+    L.nnz = nnz;
+    L.ucap = (nnz + (uint64_t)kVertexSlotsMax * n) / p.unit_entries + 2;
     L.ctl = take(sizeof(InstCtl));
     L.inst = take(sizeof(Inst));
     for (int i = 0; i < 2; ++i) {
         L.fq[i] = take((size_t)n * 4);
         L.fbeg[i] = take((size_t)n * 4);
         L.fpre[i] = take((size_t)n * 4);
+        L.flen[i] = take((size_t)n * 4);
         L.blk[i] = take((size_t)L.bcap * sizeof(Block));
         L.ustart[i] = take((size_t)L.ucap * sizeof(uint2));
     }
@@ -252,6 +261,7 @@ Inst make_inst_raw(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, c
     std::memset(&I, 0, sizeof(I));
     I.colptr = colptr;
     I.rowidx = rowidx;
+    I.nnz = L.nnz;
     I.n = n;
     I.src = src;
     I.nwords = L.nwords;
@@ -263,6 +273,7 @@ Inst make_inst_raw(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, c
         I.fq[i] = reinterpret_cast<uint32_t*>(base + L.fq[i]);
         I.fbeg[i] = reinterpret_cast<uint32_t*>(base + L.fbeg[i]);
         I.fpre[i] = reinterpret_cast<uint32_t*>(base + L.fpre[i]);
+        I.flen[i] = reinterpret_cast<uint32_t*>(base + L.flen[i]);
         I.blk[i] = reinterpret_cast<Block*>(base + L.blk[i]);
         I.ustart[i] = reinterpret_cast<uint2*>(base + L.ustart[i]);
         I.bm[i] = L.bm[i] ? reinterpret_cast<uint32_t*>(base + L.bm[i]) : nullptr;

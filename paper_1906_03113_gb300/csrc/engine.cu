@@ -131,6 +131,7 @@ __global__ void init_source_kernel(EngineArgs a) {
         // level 0 is the distinct sources, one block
         uint32_t nv = 0;
         unsigned long long w = 0;  // entry slots so far
+        unsigned long long ent = 0;  // column entries so far
         for (uint32_t b = 0; b < I.ms; ++b) {
             const uint32_t v = I.ms_src[b];
             I.ms_level[b][v] = 0;
@@ -142,7 +143,9 @@ __global__ void init_source_kernel(EngineArgs a) {
                 I.fq[0][nv] = v;
                 I.fbeg[0][nv] = I.colptr[v];
                 I.fpre[0][nv] = (uint32_t)w;
-                const unsigned long long w1 = w + len + kVertexSlots;
+                I.flen[0][nv] = len;
+                ent += len;
+                const unsigned long long w1 = w + col_slots(I, 0, I.colptr[v], len);
                 for (unsigned long long x = (w + P.unit - 1) / P.unit * P.unit; x < w1; x += P.unit)
                     I.ustart[0][x / P.unit] = make_uint2(0, nv);
                 w = w1;
@@ -155,6 +158,7 @@ __global__ void init_source_kernel(EngineArgs a) {
         I.blk[0][0].nv = nv;
         I.blk[0][0].eb = 0;
         ctl->bctr[0] = (w << kBlockBits) | 1ull;
+        ctl->fent[0] = ent;
         ctl->fcnt[0] = nv;
         ctl->reached = nv;
         w0 = w;
@@ -166,15 +170,17 @@ __global__ void init_source_kernel(EngineArgs a) {
     if (P.mode == kModeSub) I.bm[0][s >> 5] |= 1u << (s & 31);  // V_2 = V_1 \ {source}
     // frontier of level 0: one block holding the source
     const uint32_t len = I.colptr[s + 1] - I.colptr[s];
-    const uint32_t w = len + kVertexSlots;
+    const uint32_t w = col_slots(I, 0, I.colptr[s], len);
     I.fq[0][0] = s;
     I.fbeg[0][0] = I.colptr[s];
     I.fpre[0][0] = 0;
+    I.flen[0][0] = len;
     I.blk[0][0].vb = 0;
     I.blk[0][0].nv = 1;
     I.blk[0][0].eb = 0;
     for (unsigned long long x = 0; x < w; x += P.unit) I.ustart[0][x / P.unit] = make_uint2(0, 0);
     ctl->bctr[0] = ((unsigned long long)w << kBlockBits) | 1ull;
+    ctl->fent[0] = len;
     ctl->fcnt[0] = 1;
     ctl->reached = 1;
     w0 = w;

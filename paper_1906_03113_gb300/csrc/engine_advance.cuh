@@ -23,15 +23,18 @@ __device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const Eng
         if (I.sigma) I.sigma[s] = 1ull;
         if (MODE == kModeSub) atomicOr(I.bm[0] + (s >> 5), 1u << (s & 31));
         const uint32_t b0 = ld_ro(I.colptr + s);
-        const uint32_t w = ld_ro(I.colptr + s + 1) - b0 + kVertexSlots;
+        const uint32_t len = ld_ro(I.colptr + s + 1) - b0;
+        const uint32_t w = col_slots(I, 0, b0, len);
         I.fq[0][0] = s;
         I.fbeg[0][0] = b0;
         I.fpre[0][0] = 0;
+        I.flen[0][0] = len;
         I.blk[0][0].vb = 0;
         I.blk[0][0].nv = 1;
         I.blk[0][0].eb = 0;
         for (unsigned long long x = 0; x < w; x += P.unit) I.ustart[0][x / P.unit] = make_uint2(0, 0);
         st_relaxed64(&ctl->bctr[0], ((unsigned long long)w << kBlockBits) | 1ull);
+        st_relaxed64(&ctl->fent[0], (unsigned long long)len);
         st_relaxed(&ctl->fcnt[0], 1u);
         st_relaxed(&ctl->reached, 1u);
         nkind = (MODE == kModePlain) ? kPhPlainMult : kPhLevel;
@@ -77,6 +80,7 @@ __device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const Eng
                 // the buffers of level k become the "next" buffers of level k+1
                 st_relaxed(&ctl->fcnt[pc], 0u);
                 st_relaxed64(&ctl->bctr[pc], 0ull);
+                st_relaxed64(&ctl->fent[pc], 0ull);
                 if (MODE == kModePlain) st_relaxed(&ctl->tcnt, 0u);
             }
         } else {
@@ -105,8 +109,7 @@ __device__ ABFS_NOINLINE void decide_next(const Inst& I, InstCtl* ctl, const Eng
                     // hybrid direction choice from the frontier's edges m_f and the
                     // edges of vertices not reached yet m_u: bottom-up once
                     // m_f * alpha > m_u, back to top-down once n_f * beta < n
-                    const unsigned long long ne1 = ld_relaxed64(&ctl->bctr[pn]) >> kBlockBits;
-                    const unsigned long long mf = ne1 - (unsigned long long)kVertexSlots * nf;
+                    const unsigned long long mf = ld_relaxed64(&ctl->fent[pn]);
                     const unsigned long long seen = ld_relaxed64(&ctl->nnz_reached) + mf;
                     const unsigned long long nnz = ld_ro(I.colptr + I.n);
                     const unsigned long long mu = nnz > seen ? nnz - seen : 0ull;

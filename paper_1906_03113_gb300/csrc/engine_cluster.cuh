@@ -383,7 +383,7 @@ __device__ ABFS_NOINLINE uint32_t cluster_lead_run(const Inst& I, InstCtl* ctl,
     }
     __syncthreads();
     const uint32_t last = cluster_loop<MODE>(I, ctl, P, sm, k, true, heartbeat);
-    narrow_to_blocks(I, ctl, P, sm, (last + 1) & 1, sm.cr_f);
+    narrow_to_blocks(I, ctl, P, sm, last + 1, last + 1 >= sm.nr_sw ? sm.nr_mcur : sm.nr_mprev, sm.cr_f);
     if (threadIdx.x == 0) {
         st_relaxed(&ctl->reached, sm.nr_reached);
         ds_st_release(ds_addr(&sm.cbox.lock, 0), 0u);  // the cluster is free for the next run

@@ -346,6 +346,22 @@ __device__ __forceinline__ ColRef col_of(const Inst& I, uint32_t mat, uint32_t v
 __device__ __forceinline__ const uint32_t* rows_of(const Inst& I, uint32_t mat) {
     return mat == 0 ? I.rowidx : I.srows[mat - 1];
 }
+// One past the last row index of matrix mat that may be read.
+__device__ __forceinline__ const uint32_t* rows_end(const Inst& I, uint32_t mat) {
+    return mat == 0 ? I.rowidx + I.nnz : I.srows[mat - 1] + I.scap;
+}
+// Position of row index beg of matrix mat within its aligned 16-byte group
+// (the row arrays need only be 4-byte aligned).
+__device__ __forceinline__ uint32_t row_shift(const uint32_t* rows) {
+    return (uint32_t)(reinterpret_cast<uintptr_t>(rows) >> 2);
+}
+__device__ __forceinline__ uint32_t col_head(const Inst& I, uint32_t mat, uint32_t beg) {
+    return (row_shift(rows_of(I, mat)) + beg) & (kChunk - 1);
+}
+// Entry slots of a frontier vertex whose column (matrix mat) starts at beg.
+__device__ __forceinline__ uint32_t col_slots(const Inst& I, uint32_t mat, uint32_t beg, uint32_t len) {
+    return vslots(col_head(I, mat, beg), len);
+}
 
 __device__ __forceinline__ uint32_t mat_for_level(const InstCtl* ctl, uint32_t lvl) {
     // mat_cur/mat_prev/mat_switch change only between phases; the acquire at
@@ -387,6 +403,21 @@ __device__ __forceinline__ uint32_t ld_row(const uint32_t* rows, uint32_t idx, u
         asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;"
                      : "=r"(v)
                      : "l"(rows + idx), "l"(pol)
+                     : "memory");
+    return v;
+}
+
+// Four row indices from a 16-byte aligned address p, as ld_row.
+__device__ __forceinline__ uint4 ld_row4(const uint32_t* p, uint32_t mat, uint64_t pol) {
+    uint4 v;
+    if (mat == 0)
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+            : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+            : "l"(p), "l"(pol));
+    else
+        asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "l"(p), "l"(pol)
                      : "memory");
     return v;
 }

@@ -179,10 +179,10 @@ __device__ __forceinline__ void stats_flush(Smem& sm, InstCtl* ctl) {
 // work units
 // ---------------------------------------------------------------------------
 
-// Slots [lo, hi) are split evenly over the warps: warp w starts at
-// lo + w * per, per = ceil((hi - lo) / kWarps).  Staged vertex s, whose slots
+// Chunks [lo, hi) are split evenly over the warps: warp w starts at
+// lo + w * per, per = ceil((hi - lo) / kWarps).  Staged vertex s, whose chunks
 // are [st, en), records itself for every warp that starts inside its range (as
-// s - 1 when the warp starts on s's first slot, since that start bit counts
+// s - 1 when the warp starts on s's first chunk, since that start bit counts
 // again in the expand loop).  Called for every staged vertex before the loop.
 constexpr uint32_t kNoVb = 0xFFFFFFFEu;  // real values are -1 .. kTileMax - 1
 __device__ __forceinline__ uint32_t warp_share(uint32_t lo, uint32_t hi) {
@@ -199,64 +199,106 @@ __device__ __forceinline__ void mark_warp_starts(Smem& sm, uint32_t s, uint32_t 
     }
 }
 
-// Expands the slots [l0, l1) of the staged vertices (cnt of them; sm.off holds
-// their first slots, sm.off[cnt] the end; sm.sbits marks the first slots that
-// fall in [l0, l1)).  Slot s of vertex t is the column entry with row index
-// b[t] + s if s < end[t]; the kVertexSlots slots after its entries are empty.
-// The slots are split evenly over the warps; a warp takes 32 consecutive
-// slots per group (coalesced row loads) and kIlp groups per step.  The vertex
-// of slot s is a prefix count of vertex starts, read from sm.sbits with one
-// popcount.  The row loads of step s+1 are issued before step s is processed.
+// Staged vertex s, whose slots start at st (a multiple of kChunk), with
+// sm.b[s] holding its column begin and sm.end[s] its length on entry: sm.b[s]
+// becomes beg - st and sm.end[s] the end of its entry slots.  The column's
+// entries occupy slots [st + h, st + h + len), h = col_head(beg), so slot x
+// holds the row index at position b + x - h and each chunk of four slots is one
+// aligned 16-byte group of the column.
+__device__ __forceinline__ void set_slot_map(Smem& sm, const Inst& I, uint32_t mat, uint32_t s,
+                                             uint32_t st) {
+    const uint32_t beg = sm.b[s], len = sm.end[s];
+    sm.b[s] = beg - st;
+    sm.end[s] = st + col_head(I, mat, beg) + len;
+}
+
+// Expands the slots [l0, l1) (multiples of kChunk) of the staged vertices (cnt
+// of them; sm.off holds their first slots, sm.off[cnt] the end; sm.sbits has a
+// bit per chunk of [l0, l1) that starts a vertex; sm.b and sm.end as
+// set_slot_map leaves them).  The chunks are split evenly over the warps; a
+// lane takes one chunk per step, 32 consecutive chunks per warp, and reads its
+// four row indices with one 16-byte load (coalesced across the warp).  The
+// vertex of a chunk is a prefix count of vertex starts, read from sm.sbits
+// with one popcount.  The row loads of step s+1 are issued before step s is
+// processed.
 template <int MODE, int VAR>
 __device__ __forceinline__ void expand_core(const Inst& I, InstCtl* ctl, const EngineParams& P, Smem& sm,
                              uint32_t cnt, uint32_t l0, uint32_t l1, uint32_t mat,
                              uint32_t mat_next, uint32_t k, Tally& t) {
     constexpr int L = ilp_of(VAR);
+    static_assert(L == (int)kChunk, "one chunk of row indices per lane and step");
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #ifdef ABFS_EXPAND_PROFILE
     const long long xt0 = sm.prof_on ? clock64() : 0ll;
 #endif
-    const uint32_t span = l1 - l0;
+    const uint32_t c0 = l0 / kChunk, span = (l1 - l0) / kChunk;
     const uint32_t per = (span + kWarps - 1) / kWarps;
-    const uint32_t e0 = l0 + min(span, warp * per);
-    const uint32_t e1 = l0 + min(span, warp * per + per);
+    const uint32_t e0 = c0 + min(span, warp * per);
+    const uint32_t e1 = c0 + min(span, warp * per + per);
     const uint32_t* rows = rows_of(I, mat);
+    const uint32_t* const rows_hi = rows_end(I, mat);
+    const uint32_t rs = row_shift(rows);
     const uint64_t pol = evict_first_policy();
     const uint32_t le_mask = (2u << lane) - 1u;  // lanes 0..lane
-    // vertex(s) = vb + (number of vertex starts in [e0, s])
+    // vertex(c) = vb + (number of vertex starts in [e0, c])
     uint32_t vb = 0;
     if (e0 < e1) {
         vb = sm.wvb[warp];
         // recorded while staging; searched for only if the record is missing
         if (vb == kNoVb || (vb != kUnset && vb >= cnt)) {
-            uint32_t lo = 0, hi = cnt;  // off[lo] <= e0 < off[hi]
+            uint32_t lo = 0, hi = cnt;  // chunk of off[lo] <= e0 < chunk of off[hi]
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (sm.off[mid] <= e0) lo = mid;
+                if (sm.off[mid] / kChunk <= e0) lo = mid;
                 else hi = mid;
             }
-            vb = lo - (sm.off[lo] == e0 ? 1u : 0u);
+            vb = lo - (sm.off[lo] / kChunk == e0 ? 1u : 0u);
         }
     }
     uint32_t starts = 0;  // vertex starts in [e0, current group base)
-    // row index (kUnset: no entry in this slot) and frontier column of each group
+    // row indices (kUnset: no entry in this slot) and frontier column of a lane's chunk
     uint32_t r[L], j[L];
     auto load_step = [&](uint32_t base, uint32_t (&rr)[L], uint32_t (&jj)[L]) {
+        const uint32_t rel = base - c0;
+        const uint32_t sh = rel & 31;
+        uint32_t w = sm.sbits[rel >> 5] >> sh;
+        if (sh) w |= sm.sbits[(rel >> 5) + 1] << (32 - sh);
+        const uint32_t c = base + lane;
+        const uint32_t v = vb + starts + __popc(w & le_mask);
+        starts += __popc(w);
 #pragma unroll
-        for (int u = 0; u < L; ++u) {
-            const uint32_t gb = base + 32 * u;
-            const uint32_t rel = gb - l0;
-            const uint32_t sh = rel & 31;
-            uint32_t w = sm.sbits[rel >> 5] >> sh;
-            if (sh) w |= sm.sbits[(rel >> 5) + 1] << (32 - sh);
-            const uint32_t s = gb + lane;
-            const uint32_t v = vb + starts + __popc(w & le_mask);
-            starts += __popc(w);
-            rr[u] = kUnset;
-            jj[u] = 0;
-            if (s < e1 && s < sm.end[v]) {
-                jj[u] = sm.v[v];
-                rr[u] = ld_row(rows, sm.b[v] + s, mat, pol);
+        for (int q = 0; q < L; ++q) {
+            rr[q] = kUnset;
+            jj[q] = 0;
+        }
+        if (c < e1) {
+            const uint32_t s = c * kChunk;
+            const uint32_t pb = sm.b[v], hi = sm.end[v];
+            const uint32_t h = (pb + rs) & (kChunk - 1);
+            // the vertex's first chunk starts with h empty slots
+            const uint32_t lo = ((w >> lane) & 1u) ? h : 0u;
+            if (s + lo < hi) {
+                const uint32_t jv = sm.v[v];
+                // pb + s is the position of the chunk's slot h (never negative);
+                // the group may start up to three indices before the row array
+                const uint32_t* cp = rows + (pb + s) - h;
+                if (cp >= rows && cp + kChunk <= rows_hi) {
+                    const uint4 x = ld_row4(cp, mat, pol);
+                    rr[0] = x.x;
+                    rr[1] = x.y;
+                    rr[2] = x.z;
+                    rr[3] = x.w;
+#pragma unroll
+                    for (int q = 0; q < L; ++q)
+                        if ((uint32_t)q < lo || s + q >= hi) rr[q] = kUnset;
+                } else {
+                    // the group reaches past either end of the row array
+#pragma unroll
+                    for (int q = 0; q < L; ++q)
+                        if ((uint32_t)q >= lo && s + q < hi) rr[q] = ld_row(cp, q, mat, pol);
+                }
+#pragma unroll
+                for (int q = 0; q < L; ++q) jj[q] = jv;
             }
         }
     };
@@ -266,10 +308,10 @@ __device__ __forceinline__ void expand_core(const Inst& I, InstCtl* ctl, const E
     long long xt1 = 0, xflush = 0, xproc = 0;
     if (sm.prof_on) xt1 = clock64();
 #endif
-    for (uint32_t base = e0; base < e1; base += 32 * L) {
+    for (uint32_t base = e0; base < e1; base += 32) {
         uint32_t r2[L], j2[L];
-        if (base + 32 * L < e1) {
-            load_step(base + 32 * L, r2, j2);
+        if (base + 32 < e1) {
+            load_step(base + 32, r2, j2);
         } else {
 #pragma unroll
             for (int u = 0; u < L; ++u) {
@@ -427,6 +469,7 @@ __device__ ABFS_NOINLINE void unit_level(const Inst& I, InstCtl* ctl, const Engi
             const uint32_t idx = sm.seg_idx[q] + (s - sm.seg_pos[q]);
             sm.v[s] = ld_l2(I.fq[p] + idx);
             sm.b[s] = ld_l2(I.fbeg[p] + idx);
+            sm.end[s] = ld_l2(I.flen[p] + idx);
             sm.off[s] = (uint32_t)(sm.seg_eb[q] + ld_l2(I.fpre[p] + idx) - g0);
         }
         if (threadIdx.x == 0) sm.off[cnt] = (uint32_t)(sm.sub_end - g0);
@@ -434,19 +477,19 @@ __device__ ABFS_NOINLINE void unit_level(const Inst& I, InstCtl* ctl, const Engi
         // slots [lo, hi) of this sub-tile belong to the unit
         const uint32_t lo = (uint32_t)(e - g0);
         const uint32_t hi_s = (uint32_t)(min(u_hi, (unsigned long long)sm.sub_end) - g0);
-        const uint32_t nwords = (hi_s - lo + 31) / 32 + 1;
+        const uint32_t nwords = ((hi_s - lo) / kChunk + 31) / 32 + 1;
         for (uint32_t w = threadIdx.x; w < nwords; w += kThreads) sm.sbits[w] = 0u;
         __syncthreads();
         for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
             const uint32_t st = sm.off[s];
-            const uint32_t len = sm.off[s + 1] - st - kVertexSlots;
-            sm.end[s] = st + len;
-            sm.b[s] -= st;  // row index of slot x is b + x
-            mark_warp_starts(sm, s, st, st + len + kVertexSlots, lo, hi_s);
+            const uint32_t len = sm.end[s];
+            set_slot_map(sm, I, mat, s, st);
+            mark_warp_starts(sm, s, st / kChunk, sm.off[s + 1] / kChunk, lo / kChunk, hi_s / kChunk);
             if (st >= lo && st < hi_s) {
                 // the vertex's first slot lies in this unit: it joins the visited
-                // set of the next level's test (once), and starts a run of slots
-                atomicOr(&sm.sbits[(st - lo) >> 5], 1u << ((st - lo) & 31));
+                // set of the next level's test (once), and starts a run of chunks
+                const uint32_t c = (st - lo) / kChunk;
+                atomicOr(&sm.sbits[c >> 5], 1u << (c & 31));
                 const uint32_t v = sm.v[s];
                 if (MODE == kModeSub && VAR != kVarMs) atomicOr(I.bm[p ^ 1] + (v >> 5), 1u << (v & 31));
                 nnz_local += (mat == 0) ? len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));

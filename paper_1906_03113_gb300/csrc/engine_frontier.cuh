@@ -87,12 +87,13 @@ struct WarpCols {
 };
 
 // Looks the columns up once; returns the staged vertices' total weight
-// (column length + kVertexSlots each).  Whole warp.
+// (col_slots each) and, in ent, their column entries.  Whole warp.
 __device__ __forceinline__ uint32_t warp_cols(Smem& sm, const Inst& I, uint32_t mat_next, uint32_t n,
-                                              WarpCols& c) {
+                                              WarpCols& c, uint32_t& ent) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t* wv = sm.wv[threadIdx.x >> 5];
     uint32_t sum = 0;
+    ent = 0;
 #pragma unroll
     for (int it = 0; it < kWarpSpans; ++it) {
         const uint32_t i = it * 32 + lane;
@@ -102,11 +103,15 @@ __device__ __forceinline__ uint32_t warp_cols(Smem& sm, const Inst& I, uint32_t 
             const ColRef r = col_of(I, mat_next, wv[i]);
             c.beg[it] = r.beg;
             c.len[it] = r.len;
-            sum += r.len + kVertexSlots;
+            sum += col_slots(I, mat_next, r.beg, r.len);
+            ent += r.len;
         }
     }
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, d);
+    for (int d = 16; d > 0; d >>= 1) {
+        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, d);
+        ent += __shfl_xor_sync(0xFFFFFFFFu, ent, d);
+    }
     return sum;
 }
 
@@ -114,7 +119,8 @@ __device__ __forceinline__ uint32_t warp_cols(Smem& sm, const Inst& I, uint32_t 
 // block blk (entry base eb), the group starting at weight offset woff within
 // the block.  Whole warp.
 __device__ __forceinline__ void warp_emit(Smem& sm, const Inst& I, InstCtl* ctl,
-                                          const EngineParams& P, uint32_t pn, const WarpCols& c,
+                                          const EngineParams& P, uint32_t pn, uint32_t mat_next,
+                                          const WarpCols& c,
                                           uint32_t n, uint32_t blk, unsigned long long eb,
                                           uint32_t vb, uint32_t voff, uint32_t woff) {
     const uint32_t lane = threadIdx.x & 31;
@@ -124,7 +130,7 @@ __device__ __forceinline__ void warp_emit(Smem& sm, const Inst& I, InstCtl* ctl,
     for (int it = 0; it < kWarpSpans; ++it) {
         if ((uint32_t)it * 32 >= n) break;
         const uint32_t i = it * 32 + lane;
-        const uint32_t w = i < n ? c.len[it] + kVertexSlots : 0u;
+        const uint32_t w = i < n ? col_slots(I, mat_next, c.beg[it], c.len[it]) : 0u;
         const uint32_t incl = warp_incl_scan(w);
         const uint32_t pre = carry + incl - w;
         if (i < n) {
@@ -132,6 +138,7 @@ __device__ __forceinline__ void warp_emit(Smem& sm, const Inst& I, InstCtl* ctl,
             I.fq[pn][at] = wv[i];
             I.fbeg[pn][at] = c.beg[it];
             I.fpre[pn][at] = pre;
+            I.flen[pn][at] = c.len[it];
         }
         warp_unit_starts(I, ctl, P, pn, blk, voff + i, eb + pre, w);
         carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
@@ -153,10 +160,20 @@ __device__ ABFS_NOINLINE void warp_flush(
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t n = wc;
     const uint32_t* wv = sm.wv[threadIdx.x >> 5];
-    uint32_t wtot = 0;
-    for (uint32_t i = lane; i < n; i += 32) wtot += col_of(I, mat_next, wv[i]).len + kVertexSlots;
+    uint32_t wtot = 0, ent = 0;
+    for (uint32_t i = lane; i < n; i += 32) {
+        const ColRef c = col_of(I, mat_next, wv[i]);
+        wtot += col_slots(I, mat_next, c.beg, c.len);
+        ent += c.len;
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) wtot += __shfl_xor_sync(0xFFFFFFFFu, wtot, d);
+    if (P.bu_alpha) {
+        // the hybrid's direction choice needs the frontier's exact entries
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) ent += __shfl_xor_sync(0xFFFFFFFFu, ent, d);
+        if (lane == 0 && ent) atomicAdd(&ctl->fent[pn], (unsigned long long)ent);
+    }
     uint32_t blk = 0, vb = 0, ok = 0;
     unsigned long long eb = 0;
     if (lane == 0) ok = reserve_block(I, ctl, pn, n, wtot, blk, eb, vb);
@@ -176,13 +193,14 @@ __device__ ABFS_NOINLINE void warp_flush(
                 v = wv[i];
                 c = col_of(I, mat_next, v);
             }
-            const uint32_t w = i < n ? c.len + kVertexSlots : 0u;
+            const uint32_t w = i < n ? col_slots(I, mat_next, c.beg, c.len) : 0u;
             const uint32_t incl = warp_incl_scan(w);
             const uint32_t pre = carry + incl - w;
             if (i < n) {
                 I.fq[pn][vb + i] = v;
                 I.fbeg[pn][vb + i] = c.beg;
                 I.fpre[pn][vb + i] = pre;
+                I.flen[pn][vb + i] = c.len;
             }
             warp_unit_starts(I, ctl, P, pn, blk, i, eb + pre, w);
             carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
@@ -200,7 +218,9 @@ __device__ ABFS_NOINLINE void cta_flush(Smem& sm, const Inst& I, InstCtl* ctl,
     __syncthreads();
     const uint32_t n = sm.wcnt[warp];
     WarpCols c;
-    const uint32_t wtot = warp_cols(sm, I, mat_next, n, c);
+    uint32_t ent = 0;
+    const uint32_t wtot = warp_cols(sm, I, mat_next, n, c, ent);
+    if (P.bu_alpha && lane == 0 && ent) atomicAdd(&ctl->fent[pn], (unsigned long long)ent);
     if (lane == 0) {
         sm.wvoff[warp] = n;
         sm.wwoff[warp] = wtot;
@@ -226,7 +246,7 @@ __device__ ABFS_NOINLINE void cta_flush(Smem& sm, const Inst& I, InstCtl* ctl,
     }
     __syncthreads();
     if (sm.gblk != kUnset && n)
-        warp_emit(sm, I, ctl, P, pn, c, n, sm.gblk, sm.geb, sm.gbase, sm.wvoff[warp],
+        warp_emit(sm, I, ctl, P, pn, mat_next, c, n, sm.gblk, sm.geb, sm.gbase, sm.wvoff[warp],
                   sm.wwoff[warp]);
     if (lane == 0) sm.wcnt[warp] = 0;
     __syncthreads();
@@ -272,11 +292,11 @@ __device__ __forceinline__ void narrow_append(Smem& sm, const Inst& I, InstCtl* 
                 if (at < I.n) {
                     I.fq[pn][at] = v[q];
                     I.fbeg[pn][at] = c[q].beg;
-                    I.fpre[pn][at] = c[q].len;
+                    I.flen[pn][at] = c[q].len;
                 } else {
                     fail(ctl, 7);
                 }
-                wsum += c[q].len + kVertexSlots;
+                wsum += col_slots(I, mat_next, c[q].beg, c[q].len);
             }
         }
     }

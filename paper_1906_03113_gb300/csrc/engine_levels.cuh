@@ -71,16 +71,16 @@ __device__ __forceinline__ bool shrink_due(const EngineParams& P, uint32_t reach
 // ---------------------------------------------------------------------------
 // While a search's frontier stays within narrow_max vertices and narrow_edges
 // slots, one CTA runs its levels back to back without the block bookkeeping of
-// wide levels.  The frontier of level k is a plain list at fq/fbeg/fpre[k&1]:
+// wide levels.  The frontier of level k is a plain list at fq/fbeg/flen[k&1]:
 // vertex, column begin and column length.  Claims gather in the warp staging
 // buffers and are appended with a shared-memory counter; the reached count
 // and the level stay in shared memory until the run ends.  The run ends when
 // the frontier empties, outgrows the narrow bounds, or a shrink is due; the
 // last frontier is then rewritten as blocks and the general path decides what
-// follows.
+// follows.  (fpre is unused until the blocks are written.)
 
 // Expands the f vertices at [base, base + f) of the level-k list (lens:
-// fbeg/fpre hold column begins and lengths in matrix mat; otherwise only the
+// fbeg/flen hold column begins and lengths in matrix mat; otherwise only the
 // ids are valid and the columns are looked up) in chunks of up to `tile`
 // vertices and windows of up to kUnitMax slots.  Whole CTA.
 template <int MODE>
@@ -97,7 +97,7 @@ __device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const
             uint32_t beg, len;
             if (lens) {
                 beg = ld_l2(I.fbeg[p] + at);
-                len = ld_l2(I.fpre[p] + at);
+                len = ld_l2(I.flen[p] + at);
             } else {
                 const ColRef c = col_of(I, mat, v);
                 beg = c.beg;
@@ -105,7 +105,8 @@ __device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const
             }
             sm.v[s] = v;
             sm.b[s] = beg;
-            sm.off[s] = len + kVertexSlots;
+            sm.end[s] = len;
+            sm.off[s] = col_slots(I, mat, beg, len);
             // the frontier joins the visited set of the next level's test
             if (MODE == kModeSub) atomicOr(I.bm[p ^ 1] + (v >> 5), 1u << (v & 31));
             nnz_local += (mat == 0) ? len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
@@ -119,10 +120,12 @@ __device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const
         uint32_t l0 = 0, l1 = min(S, kUnitMax);
         for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
             const uint32_t st = sm.off[s], en = sm.off[s + 1];
-            sm.end[s] = en - kVertexSlots;
-            sm.b[s] -= st;  // row index of slot x is b + x
-            if (st < l1) atomicOr(&sm.sbits[st >> 5], 1u << (st & 31));
-            mark_warp_starts(sm, s, st, en, l0, l1);
+            set_slot_map(sm, I, mat, s, st);
+            if (st < l1) {
+                const uint32_t c = st / kChunk;
+                atomicOr(&sm.sbits[c >> 5], 1u << (c & 31));
+            }
+            mark_warp_starts(sm, s, st / kChunk, en / kChunk, l0 / kChunk, l1 / kChunk);
         }
         __syncthreads();
         prof_add(sm, kProfNLoad, pt0);
@@ -139,8 +142,11 @@ __device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const
             __syncthreads();
             for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
                 const uint32_t st = sm.off[s];
-                if (st >= l0 && st < l1) atomicOr(&sm.sbits[(st - l0) >> 5], 1u << ((st - l0) & 31));
-                mark_warp_starts(sm, s, st, sm.off[s + 1], l0, l1);
+                if (st >= l0 && st < l1) {
+                    const uint32_t c = (st - l0) / kChunk;
+                    atomicOr(&sm.sbits[c >> 5], 1u << (c & 31));
+                }
+                mark_warp_starts(sm, s, st / kChunk, sm.off[s + 1] / kChunk, l0 / kChunk, l1 / kChunk);
             }
             __syncthreads();
         }
@@ -174,7 +180,7 @@ __device__ ABFS_NOINLINE bool narrow_expand_short(const Inst& I, InstCtl* ctl, c
         v = ld_l2(I.fq[p] + at);
         if (lens) {
             beg = ld_l2(I.fbeg[p] + at);
-            len = ld_l2(I.fpre[p] + at);
+            len = ld_l2(I.flen[p] + at);
         } else {
             const ColRef c = col_of(I, mat, v);
             beg = c.beg;
@@ -266,8 +272,8 @@ __device__ ABFS_NOINLINE bool narrow_expand_short(const Inst& I, InstCtl* ctl, c
                     if (MODE == kModeSub) {
                         I.fq[pn][at] = r[j];
                         I.fbeg[pn][at] = nb[j];
-                        I.fpre[pn][at] = nl[j];
-                        slots += nl[j] + kVertexSlots;
+                        I.flen[pn][at] = nl[j];
+                        slots += col_slots(I, mat_next, nb[j], nl[j]);
                         // the next level reads this column: start bringing it to L2
                         if (nl[j]) {
                             const uint32_t* c = rows_of(I, mat_next) + nb[j];
@@ -293,13 +299,20 @@ __device__ ABFS_NOINLINE bool narrow_expand_short(const Inst& I, InstCtl* ctl, c
     return true;
 }
 
-// Rewrites the list of parity pn (fn vertices; fpre holds column lengths) as
+// Rewrites the list of level kl (fn vertices; columns in matrix mat) as
 // frontier blocks of up to kWarps*kWarpBuf vertices: slot offsets within the
 // block, unit starts, and the parity's counters.  The warp staging buffers
 // (empty here) stage each chunk so global reads and writes stay coalesced.
 // Whole CTA.
 __device__ ABFS_NOINLINE void narrow_to_blocks(const Inst& I, InstCtl* ctl, const EngineParams& P,
-                                               Smem& sm, uint32_t pn, uint32_t fn) {
+                                               Smem& sm, uint32_t kl, uint32_t mat, uint32_t fn) {
+    const uint32_t pn = kl & 1;
+    // the hybrid's direction choice needs the list's exact entries
+    if (P.bu_alpha) {
+        if (threadIdx.x == 0) st_relaxed64(&ctl->fent[pn], 0ull);
+        __syncthreads();
+    }
+    uint32_t ent = 0;
     constexpr uint32_t kChunk = kWarps * kWarpBuf;
     constexpr uint32_t kItems = kChunk / kThreads;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -308,14 +321,18 @@ __device__ ABFS_NOINLINE void narrow_to_blocks(const Inst& I, InstCtl* ctl, cons
     uint32_t nb = 0;
     for (uint32_t c0 = 0; c0 < fn; c0 += kChunk, ++nb) {
         const uint32_t cnt = min(kChunk, fn - c0);
-        for (uint32_t i = tid; i < cnt; i += kThreads) buf[i] = ld_l2(I.fpre[pn] + c0 + i);
+        for (uint32_t i = tid; i < cnt; i += kThreads) {
+            const uint32_t len = ld_l2(I.flen[pn] + c0 + i);
+            buf[i] = col_slots(I, mat, ld_l2(I.fbeg[pn] + c0 + i), len);
+            ent += len;
+        }
         __syncthreads();
         uint32_t x[kItems];
         uint32_t sum = 0;
 #pragma unroll
         for (uint32_t q = 0; q < kItems; ++q) {
             const uint32_t idx = tid * kItems + q;
-            x[q] = idx < cnt ? buf[idx] + kVertexSlots : 0u;
+            x[q] = idx < cnt ? buf[idx] : 0u;
             sum += x[q];
         }
         const uint32_t incl = warp_incl_scan(sum);
@@ -352,6 +369,11 @@ __device__ ABFS_NOINLINE void narrow_to_blocks(const Inst& I, InstCtl* ctl, cons
         }
         eb += total;
         __syncthreads();  // buf and warp_sums are reused
+    }
+    if (P.bu_alpha) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) ent += __shfl_xor_sync(0xFFFFFFFFu, ent, d);
+        if (lane == 0 && ent) atomicAdd(&ctl->fent[pn], (unsigned long long)ent);
     }
     if (tid == 0) {
         st_relaxed64(&ctl->bctr[pn], (eb << kBlockBits) | (unsigned long long)nb);
@@ -479,7 +501,7 @@ __device__ ABFS_NOINLINE uint32_t narrow_run(const Inst& I, InstCtl* ctl, const 
     for (int d = 16; d > 0; d >>= 1) nnz_local += __shfl_xor_sync(0xFFFFFFFFu, nnz_local, d);
     if (lane == 0 && nnz_local) atomicAdd(&sm.st_nnz, (unsigned long long)nnz_local);
     tally_flush(sm, t);
-    narrow_to_blocks(I, ctl, P, sm, (k + 1) & 1, sm.nr_f);
+    narrow_to_blocks(I, ctl, P, sm, k + 1, k + 1 >= sw ? mat_cur : mat_prev, sm.nr_f);
     if (threadIdx.x == 0) st_relaxed(&ctl->reached, sm.nr_reached);
     stats_flush(sm, ctl);
     prof_add(sm, kProfNBlocks, pt4);

@@ -53,13 +53,25 @@ constexpr int kWarpFlushAt = kWarpBuf - 32 * kIlp;
 #endif
 constexpr uint32_t kUnitMax = ABFS_UNIT_MAX;
 static_assert((kUnitMax & (kUnitMax - 1)) == 0 && kUnitMax >= 1024, "unit size");
-constexpr int kStartWords = kUnitMax / 32 + 2;
+// The expand loop reads row indices four at a time (one 16-byte load per
+// lane): slots come in chunks of four, and the start bitmap has a bit per chunk.
+constexpr uint32_t kChunk = 4;
+constexpr int kStartWords = kUnitMax / kChunk / 32 + 2;
 // Marker of an unset parent / unclaimed vertex (reads as -1 through int32).
 constexpr uint32_t kUnset = 0xFFFFFFFFu;
 // Weight of a frontier vertex in its level's work space: its column length
 // plus kVertexSlots, so units balance vertices as well as entries and a
-// vertex without entries still owns a slot.
+// vertex without entries still owns a slot, rounded so that every vertex
+// starts on a chunk boundary.  Entry x of a column whose first row index sits
+// at position h of its aligned 16-byte group occupies slot start + h + x, so
+// every chunk of four slots maps onto one aligned 16-byte group of the
+// column's row indices.
 constexpr uint32_t kVertexSlots = 2;
+__host__ __device__ constexpr uint32_t vslots(uint32_t h, uint32_t len) {
+    return ((h & (kChunk - 1)) + len + kVertexSlots + kChunk - 1) & ~(kChunk - 1);
+}
+// Upper bound of vslots(h, len) - len.
+constexpr uint32_t kVertexSlotsMax = 2 * (kChunk - 1) + kVertexSlots;
 // Packed frontier counter: [entries : 40 bits][blocks : 24 bits].
 constexpr uint32_t kBlockBits = 24;
 constexpr uint32_t kBlockMask = (1u << kBlockBits) - 1u;
@@ -103,6 +115,7 @@ struct InstCtl {
     unsigned long long grab;     // [epoch:32][units taken:32] of the published phase
     unsigned long long desc[2];  // per epoch parity: [epoch:32][units:32]
     unsigned long long bctr[2];  // per level parity: [entries:40][blocks:24] of the frontier
+    unsigned long long fent[2];  // per level parity: column entries of the frontier (hybrid only)
     uint32_t pending[2];         // per epoch parity: units not yet completed
     uint32_t kind[2];            // per epoch parity: PhaseKind
     uint32_t plevel[2];          // per epoch parity: BFS level of the phase
@@ -134,6 +147,7 @@ struct InstCtl {
 struct Inst {
     const uint32_t* colptr;  // input CSC
     const uint32_t* rowidx;
+    unsigned long long nnz;  // row indices at rowidx (reads stay inside them)
     uint32_t n;
     uint32_t src;
     uint32_t nwords;         // ceil(n/32)
@@ -150,6 +164,7 @@ struct Inst {
     uint32_t* fq[2];         // frontier vertices, by level parity
     uint32_t* fbeg[2];       // their column begins (kUnset: no entries)
     uint32_t* fpre[2];       // their entry offsets within their block
+    uint32_t* flen[2];       // their column lengths
     Block* blk[2];           // frontier blocks
     uint2* ustart[2];        // unit u starts in (block, vertex index in block)
     unsigned long long* y;   // comparator: stamped (min, index) accumulator
@@ -243,7 +258,8 @@ enum ProfSlot : int {
 
 // Per-search workspace layout: byte offsets of each buffer from the base.
 struct Layout {
-    size_t bm[2], fbm[2], fq[2], fbeg[2], fpre[2], blk[2], ustart[2], y, touched, sbeg[2], slen[2],
+    uint64_t nnz;
+    size_t bm[2], fbm[2], fq[2], fbeg[2], fpre[2], flen[2], blk[2], ustart[2], y, touched, sbeg[2], slen[2],
         srows[2], ctl, inst;
     size_t ms_vis, ms_fr[2], ms_nx, ms_src, ms_lev, ms_par;  // multi-source searches only
     size_t total;

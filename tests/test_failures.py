@@ -30,8 +30,8 @@ class FailingHook:
     the blocks it handed out and got back.  host=True hands out host memory
     (for host-only error paths on a machine without a GPU)."""
 
-    def __init__(self, fail_at: int, host: bool):
-        self.fail_at, self.host = fail_at, host
+    def __init__(self, fail_at: int, host: bool, shift: int = 0):
+        self.fail_at, self.host, self.shift = fail_at, host, shift
         self.calls = 0
         self.live = {}
         if host:
@@ -47,7 +47,7 @@ class FailingHook:
         if self.fail_at and self.calls >= self.fail_at:
             return None
         if self.host:
-            p = self.libc.malloc(nbytes)
+            p = self.libc.malloc(nbytes + 16) + self.shift
         else:
             import torch
             t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
@@ -60,7 +60,7 @@ class FailingHook:
     def _free(self, p, ctx):
         obj = self.live.pop(p)
         if self.host:
-            self.libc.free(p)
+            self.libc.free(p - self.shift)
         del obj
 
     def install(self, lib):
@@ -99,6 +99,23 @@ def test_allocator_failure_on_the_host_path(lib):
             FailingHook.remove(lib)
         assert rc == binding.ERR_OOM and not out.value
         assert hook.calls == n_fail and not hook.live
+
+
+def test_allocator_blocks_off_16_byte_alignment_are_refused(lib):
+    """A hook block that is not 16-byte aligned goes back to the hook and the
+    call fails with ABFS_ERR_INVALID_ARG before anything reads it."""
+    cp = (ctypes.c_uint32 * 3)(0, 1, 2)
+    rows = (ctypes.c_uint32 * 2)(1, 0)
+    for shift in (4, 8):
+        hook = FailingHook(0, host=True, shift=shift)
+        hook.install(lib)
+        try:
+            out = ctypes.c_void_p()
+            rc = lib.abfs_graph_create(cp, rows, 2, 2, 0, 0, None, ctypes.byref(out))
+        finally:
+            FailingHook.remove(lib)
+        assert rc == binding.ERR_INVALID_ARG and not out.value
+        assert hook.calls == 1 and not hook.live
 
 
 # ---------------------------------------------------------------------------
