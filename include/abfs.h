@@ -119,8 +119,9 @@ typedef struct {
                                  CTAs are idle. */
     uint32_t cluster_max;     /* a cluster run continues while a level has <= this many
                                  frontier vertices ... */
-    uint32_t cluster_edges;   /* ... and <= this many entry slots (column entries + 2 per
-                                 vertex) */
+    uint32_t cluster_edges;   /* ... and <= this many entry slots (column entries plus
+                                 up to 6 per vertex, so that each vertex starts on a group
+                                 of four) */
     uint32_t multi_source;    /* batches (submatrix mode, no path counts): when at least
                                  this many queries search one undirected graph, they run as
                                  multi-source searches of up to 64 sources each -- one
@@ -234,8 +235,8 @@ int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_host, int32_t*
  *   further level of a resident narrow run, 3 if it is a further level of a
  *   cluster run ([4] then holds the run's CTAs), [4] units or touched rows of
  *   the phase, [5] frontier
- *   vertices, [6] entry slots of that frontier (column entries + 2 per
- *   vertex, low 32 bits), [7] 0.  For a level, [4] is its number of work
+ *   vertices, [6] entry slots of that frontier (column entries plus up to 6
+ *   per vertex, low 32 bits), [7] 0.  For a level, [4] is its number of work
  *   units (comparator mask: touched rows).
  * *count receives the number written.  Synchronises `stream`.
  */
@@ -387,7 +388,7 @@ int abfs_serve_stop(abfs_server_t s, abfs_serve_report* report);
  * ABFS_ERR_CUDA when the device is out of memory: make it at start-up, before
  * the memory is budgeted or an allocator is locked.  Later calls allocate
  * nothing.  The scratch a search needs is about 65 bytes per vertex plus 16
- * bytes per 1024 entry slots (column entries + at most 8 per vertex); graphs
+ * bytes per 1024 entry slots (column entries + at most 6 per vertex); graphs
  * whose scratch exceeds the array (72 MiB - 256 bytes), e.g. beyond about 1.1
  * million vertices at average degree 16, are rejected.
  * Every call uses the same array, which keeps the previous call's contents;

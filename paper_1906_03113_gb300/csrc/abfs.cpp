@@ -138,7 +138,7 @@ abfs_params default_params() {
     p.cluster_ctas = 8;
     p.cluster_min = 2048;
     p.cluster_max = 16384;
-    p.cluster_edges = 1u << 15;
+    p.cluster_edges = 1u << 16;
     p.multi_source = 8;
     return p;
 }

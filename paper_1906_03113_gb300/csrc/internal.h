@@ -59,19 +59,19 @@ constexpr uint32_t kChunk = 4;
 constexpr int kStartWords = kUnitMax / kChunk / 32 + 2;
 // Marker of an unset parent / unclaimed vertex (reads as -1 through int32).
 constexpr uint32_t kUnset = 0xFFFFFFFFu;
-// Weight of a frontier vertex in its level's work space: its column length
-// plus kVertexSlots, so units balance vertices as well as entries and a
-// vertex without entries still owns a slot, rounded so that every vertex
-// starts on a chunk boundary.  Entry x of a column whose first row index sits
-// at position h of its aligned 16-byte group occupies slot start + h + x, so
-// every chunk of four slots maps onto one aligned 16-byte group of the
-// column's row indices.
-constexpr uint32_t kVertexSlots = 2;
+// Weight of a frontier vertex in its level's work space: the chunks that hold
+// its column.  Entry x of a column whose first row index sits at position h of
+// its aligned 16-byte group occupies slot start + h + x, and every vertex
+// starts on a chunk boundary, so every chunk of four slots maps onto one
+// aligned 16-byte group of the column's row indices.  A vertex owns at least
+// one chunk (a vertex without entries still owns a start), so units balance
+// vertices as well as entries.
 __host__ __device__ constexpr uint32_t vslots(uint32_t h, uint32_t len) {
-    return ((h & (kChunk - 1)) + len + kVertexSlots + kChunk - 1) & ~(kChunk - 1);
+    return (h & (kChunk - 1)) + len == 0 ? kChunk
+                                         : ((h & (kChunk - 1)) + len + kChunk - 1) / kChunk * kChunk;
 }
 // Upper bound of vslots(h, len) - len.
-constexpr uint32_t kVertexSlotsMax = 2 * (kChunk - 1) + kVertexSlots;
+constexpr uint32_t kVertexSlotsMax = 2 * (kChunk - 1);
 // Packed frontier counter: [entries : 40 bits][blocks : 24 bits].
 constexpr uint32_t kBlockBits = 24;
 constexpr uint32_t kBlockMask = (1u << kBlockBits) - 1u;

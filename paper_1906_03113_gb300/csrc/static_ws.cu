@@ -24,7 +24,7 @@ namespace {
 
 // 72 MiB: enough for graphs up to about 1.1 million vertices (the layout
 // needs about 65 bytes per vertex plus two unit-start tables of 8 bytes per
-// 1024 entry slots, i.e. 16 bytes per 1024 of nnz + 8n).
+// 1024 entry slots, i.e. 16 bytes per 1024 of nnz + 6n).
 constexpr size_t kStaticWorkspaceBytes = 72ull << 20;
 // The first 256 bytes hold the launch's completion counter and heartbeat.
 constexpr size_t kStaticHeader = 256;
