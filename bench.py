@@ -791,7 +791,7 @@ def main():
         # batched: 64 sources in one persistent launch (CUDA graph replay)
         if args.workload == "rmat22":
             bs = synth.sources_with_degree(g, 64, seed=2)
-            plan = abfs.BatchPlan([G] * 64, bs)
+            plan = abfs.BatchPlan([G] * 64, bs, params=params)
             plan.launch()
             torch.cuda.synchronize()
             assert all(x == 0 for x in plan.status())

@@ -284,8 +284,10 @@ int abfs_batch_destroy(abfs_batch_t b);
 
 /*
  * Autotuner: times candidate parameter sets on `count` searches from
- * `sources` and stores the fastest in the graph (used when params = NULL).
- * `mode` selects which method is tuned.  *best (may be NULL) receives the
+ * `sources`.  `mode` selects which method is tuned; for the submatrix method
+ * the fastest set is also stored in the graph and used when params = NULL (a
+ * tuned comparator set is only returned, so NULL params keep meaning the
+ * submatrix method).  *best (may be NULL) receives the
  * choice and *best_ms its mean device time per search.  With `cache_path`
  * non-NULL the result is read from / appended to that JSON-lines file, keyed
  * by GPU name, SM count, mode and the graph's size class.  Synchronises.

@@ -1075,8 +1075,10 @@ extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count
             p.mode = mode;
             if (check_params(p) == ABFS_OK) {
                 std::lock_guard<std::mutex> lk(g->mu);
-                g->tuned = true;
-                g->tuned_params = p;
+                if (mode == ABFS_MODE_SUBMATRIX) {
+                    g->tuned = true;
+                    g->tuned_params = p;
+                }
                 if (best) *best = p;
                 if (best_ms && json_num(found, "ms", &v)) *best_ms = (float)v;
                 return ABFS_OK;
@@ -1157,8 +1159,10 @@ extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count
     if (rc) return rc;
     {
         std::lock_guard<std::mutex> lk(g->mu);
-        g->tuned = true;
-        g->tuned_params = best_p;
+        if (mode == ABFS_MODE_SUBMATRIX) {
+            g->tuned = true;
+            g->tuned_params = best_p;
+        }
     }
     if (best) *best = best_p;
     if (best_ms) *best_ms = best_time;

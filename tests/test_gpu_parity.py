@@ -310,6 +310,12 @@ def test_tune_keeps_results(small, tmp_path):
     assert best2.as_dict() == best.as_dict()
     level, parent = abfs.run(dev["rmat_14"], srcs[0])          # uses the tuned params
     _check(g, srcs[0], level, parent, "tuned")
+    # tuning the comparator leaves the graph's default (submatrix) set alone:
+    # without params a search still masks before it multiplies
+    abfs.tune(dev["rmat_14"], srcs, PLAIN)
+    level, parent, st = abfs.run(dev["rmat_14"], srcs[0], stats=True)
+    _check(g, srcs[0], level, parent, "tuned after a comparator tune")
+    assert st["entries_unmasked"] < st["entries_read"], st
 
 
 def test_batch_tune_picks_a_valid_set(small, tmp_path):
