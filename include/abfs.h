@@ -224,6 +224,22 @@ int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_host, int32_t*
                   abfs_stream_t stream, const abfs_params* params, abfs_stats* stats);
 
 /*
+ * `count` searches of Algorithm 1 from sources[0..count), end to end through
+ * host memory: search i writes level_host[i*n .. i*n+n) and
+ * parent_host[i*n .. i*n+n) (HOST buffers of count*n int32 each; pinned
+ * memory lets the copies overlap the searches).  The searches run one after
+ * another on `stream` into two alternating device buffers; while search i+1
+ * runs, the outputs of search i travel to the host on a copy stream of the
+ * graph's own, so the copies cost no search time when they take less time
+ * than a search.  status (host, count entries; may be NULL) receives each
+ * search's own status.  Synchronises; returns the first non-zero status,
+ * ABFS_ERR_INVALID_ARG (checked before anything runs) if a source is >= n.
+ */
+int abfs_run_host_many(abfs_graph_t g, const uint32_t* sources, uint32_t count,
+                       int32_t* level_host, int32_t* parent_host, abfs_stream_t stream,
+                       const abfs_params* params, int32_t* status);
+
+/*
  * abfs_run plus a per-phase trace of the search, for profiling: trace_host
  * receives up to `cap` entries of 8 uint32 each --
  *   [0..1] %globaltimer (ns, low/high), [2] phase kind << 24 | BFS level

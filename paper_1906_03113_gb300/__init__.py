@@ -26,6 +26,7 @@ from .binding import (  # noqa: F401
     calibrate,
     run_batch,
     run_host,
+    run_host_many,
     run_trace,
     strerror,
     tune,

@@ -157,6 +157,7 @@ def load():
         "abfs_run_counts": ([vp, u32, vp, vp, vp, vp, P(Params), P(Stats)], c_int),
         "abfs_calibrate": ([u32, P(Calibration), vp], c_int),
         "abfs_run_host": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
+        "abfs_run_host_many": ([vp, P(u32), u32, vp, vp, vp, P(Params), P(i32)], c_int),
         "abfs_run_trace": ([vp, u32, vp, vp, vp, P(Params), vp, u32, P(u32)], c_int),
         "abfs_run_batch": ([P(vp), P(u32), u32, P(vp), P(vp), vp, P(Params), P(i32)], c_int),
         "abfs_batch_create": ([P(vp), P(u32), u32, P(vp), P(vp), P(Params), vp, P(vp)], c_int),
@@ -388,6 +389,30 @@ def run_host(g: Graph, source: int, level_host: np.ndarray | None = None,
                               ctypes.byref(st) if st else None)
     _check(rc, "abfs_run_host")
     return (level_host, parent_host, st.as_dict()) if stats else (level_host, parent_host)
+
+
+def run_host_many(g: Graph, sources, level_host=None, parent_host=None, stream=None,
+                  params: Params | None = None):
+    """abfs_run_host_many: search i's results in row i of host arrays of shape
+    (len(sources), n) (pinned tensors let the copies overlap the searches).
+    Returns (level_host, parent_host, per-search statuses)."""
+    srcs = np.ascontiguousarray(np.asarray(sources, dtype=np.uint32))
+    count = int(srcs.shape[0])
+    if level_host is None:
+        level_host = np.empty((count, g.n), dtype=np.int32)
+    if parent_host is None:
+        parent_host = np.empty((count, g.n), dtype=np.int32)
+    lp = level_host.ctypes.data if isinstance(level_host, np.ndarray) else level_host.data_ptr()
+    pp = parent_host.ctypes.data if isinstance(parent_host, np.ndarray) else parent_host.data_ptr()
+    st = (ctypes.c_int32 * max(count, 1))()
+    rc = load().abfs_run_host_many(g.handle, srcs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                   count, lp, pp, _stream_ptr(stream),
+                                   ctypes.byref(params) if params else None, st)
+    statuses = [int(st[i]) for i in range(count)]
+    # a search's own failure comes back in `statuses`; anything else raises
+    if rc and rc != next((x for x in statuses if x), 0):
+        _check(rc, "abfs_run_host_many")
+    return level_host, parent_host, statuses
 
 
 def _ptr_array(ptrs):

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -342,6 +343,15 @@ struct abfs_graph_s {
     int32_t* d_parent = nullptr;
     cudaEvent_t last_use = nullptr;
     bool used = false;
+    // abfs_run_host_many: a second pair of device outputs, the stream that copies
+    // one search's outputs out while the next one runs, and pinned status words
+    int32_t* d_level2 = nullptr;
+    int32_t* d_parent2 = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t computed[2] = {nullptr, nullptr};
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    uint32_t* h_status = nullptr;  // two words (status, err) per search
+    uint32_t h_status_cap = 0;     // searches h_status holds
 };
 
 namespace {
@@ -577,8 +587,17 @@ extern "C" int abfs_graph_destroy(abfs_graph_t g) {
     if (!g) return ABFS_ERR_INVALID_ARG;
     if (g->used && g->last_use) cudaEventSynchronize(g->last_use);
     free_workspace(g->ws);
+    if (g->copy_stream) cudaStreamSynchronize(g->copy_stream);
     dev_free(g->d_level);
     dev_free(g->d_parent);
+    dev_free(g->d_level2);
+    dev_free(g->d_parent2);
+    for (int b = 0; b < 2; ++b) {
+        if (g->computed[b]) cudaEventDestroy(g->computed[b]);
+        if (g->copied[b]) cudaEventDestroy(g->copied[b]);
+    }
+    if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+    if (g->h_status) cudaFreeHost(g->h_status);
     dev_free(g->d_colptr);
     dev_free(g->d_rowidx);
     dev_free(g->d_inb);
@@ -659,6 +678,79 @@ extern "C" int abfs_run_host(abfs_graph_t g, uint32_t source, int32_t* level_hos
     // the call synchronises anyway: it returns the search's own status
     abfs_stats local;
     return finish_stats(g, s, stats ? stats : &local);
+}
+
+extern "C" int abfs_run_host_many(abfs_graph_t g, const uint32_t* sources, uint32_t count,
+                                  int32_t* level_host, int32_t* parent_host, abfs_stream_t stream,
+                                  const abfs_params* params, int32_t* status) {
+    if (!g || (count && (!sources || !level_host || !parent_host))) return ABFS_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < count; ++i)
+        if (sources[i] >= g->n) return ABFS_ERR_INVALID_ARG;
+    if (count == 0) return ABFS_OK;
+    abfs_params tmp;
+    const abfs_params& p = pick_params(g, params, tmp);
+    int rc = check_params(p);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    const size_t nb = (size_t)g->n * 4;
+    if (!g->d_level) {
+        rc = dev_alloc((void**)&g->d_level, nb);
+        if (!rc) rc = dev_alloc((void**)&g->d_parent, nb);
+        if (rc) return rc;
+    }
+    if (!g->d_level2) {
+        rc = dev_alloc((void**)&g->d_level2, nb);
+        if (!rc) rc = dev_alloc((void**)&g->d_parent2, nb);
+        if (rc) return rc;
+    }
+    if (!g->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            CK(cudaEventCreateWithFlags(&g->computed[b], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&g->copied[b], cudaEventDisableTiming));
+        }
+    }
+    if (g->h_status_cap < count) {
+        if (g->h_status) cudaFreeHost(g->h_status);
+        g->h_status = nullptr;
+        g->h_status_cap = 0;
+        if (cudaMallocHost((void**)&g->h_status, (size_t)count * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return ABFS_ERR_OOM;
+        }
+        g->h_status_cap = count;
+    }
+    int32_t* const dl[2] = {g->d_level, g->d_level2};
+    int32_t* const dp[2] = {g->d_parent, g->d_parent2};
+    cudaStream_t c = g->copy_stream;
+    // search i writes buffer pair i & 1; its outputs leave on the copy stream
+    // while search i + 1 runs, and search i + 2 waits until they have left
+    for (uint32_t i = 0; i < count; ++i) {
+        const int b = (int)(i & 1u);
+        if (i >= 2) CK(cudaStreamWaitEvent(s, g->copied[b], 0));
+        rc = enqueue_single(g, sources[i], dl[b], dp[b], s, p);
+        if (rc) break;
+        const char* ctl = g->ws.base + g->ws.L.ctl;
+        CK(cudaMemcpyAsync(g->h_status + 2 * (size_t)i, ctl + offsetof(InstCtl, status), 8,
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(g->computed[b], s));
+        CK(cudaStreamWaitEvent(c, g->computed[b], 0));
+        CK(cudaMemcpyAsync(level_host + (size_t)i * g->n, dl[b], nb, cudaMemcpyDeviceToHost, c));
+        CK(cudaMemcpyAsync(parent_host + (size_t)i * g->n, dp[b], nb, cudaMemcpyDeviceToHost, c));
+        CK(cudaEventRecord(g->copied[b], c));
+    }
+    CK(cudaStreamSynchronize(c));
+    CK(cudaStreamSynchronize(s));
+    if (rc) return rc;
+    int first = ABFS_OK;
+    for (uint32_t i = 0; i < count; ++i) {
+        const uint32_t st = g->h_status[2 * (size_t)i], err = g->h_status[2 * (size_t)i + 1];
+        const int v = (st == kDone) ? ABFS_OK : (err ? (int)err : ABFS_ERR_DEVICE);
+        if (status) status[i] = v;
+        if (v && !first) first = v;
+    }
+    return first;
 }
 
 extern "C" int abfs_run_trace(abfs_graph_t g, uint32_t source, int32_t* level, int32_t* parent,

@@ -218,6 +218,34 @@ def test_run_host_matches(small):
     _check(g, s, lev_h, par_h, "run_host")
 
 
+def test_run_host_many_matches(small):
+    """Many searches into host memory: two device buffers alternate and each
+    search's outputs are copied out while the next one runs, so the third and
+    fourth searches reuse buffers whose copies had to finish first."""
+    gs, dev = small
+    for name in ("rmat_14", "rgg_2_15"):
+        g = gs[name]
+        base = _sources(g)
+        srcs = [base[0], base[-1], base[1 % len(base)], base[0], base[-1]]
+        for count in (1, 2, len(srcs)):
+            lev = torch.full((count, g.n), 7, dtype=torch.int32).pin_memory()
+            par = torch.full((count, g.n), 7, dtype=torch.int32).pin_memory()
+            _, _, st = abfs.run_host_many(dev[name], srcs[:count], lev, par)
+            assert st == [0] * count, st
+            for i, s in enumerate(srcs[:count]):
+                _check(g, s, lev[i], par[i], f"run_host_many {name} {count} #{i}")
+    # pageable host arrays work too (the copies then do not overlap)
+    g = gs["rmat_14"]
+    base = _sources(g)
+    lev, par, st = abfs.run_host_many(dev["rmat_14"], base[:3])
+    assert st == [0, 0, 0]
+    for i, s in enumerate(base[:3]):
+        _check(g, s, lev[i], par[i], "run_host_many pageable")
+    with pytest.raises(abfs.AbfsError) as ei:
+        abfs.run_host_many(dev["rmat_14"], [0, g.n])
+    assert ei.value.status == 1
+
+
 def test_repeated_runs_identical(small):
     gs, dev = small
     g = gs["rmat_14"]
