@@ -2,9 +2,9 @@
 //
 // One launch runs one or many searches to completion.  Every search advances
 // level by level (Algorithm 1, Section 8).  The frontier x_k is kept as a list
-// of vertices in blocks; every vertex carries a weight (its column length plus
-// two vertex slots), and the level's column entries form one "entry space" of
-// sum(weights) slots.  Work units are ranges of that space, sized per level to
+// of vertices in blocks; every vertex carries a weight (the 4-slot chunks that
+// hold its column, each chunk one aligned 16-byte group of row indices), and
+// the level's column entries form one "entry space" of sum(weights) slots.  Work units are ranges of that space, sized per level to
 // about two per CTA, so a unit holds the same number of entries whether it
 // covers one hub column or thousands of short ones (the PRAM "one processor per nonzero" of Theorem 4,
 // with load balance instead of a processor per entry).  Any CTA may take any
