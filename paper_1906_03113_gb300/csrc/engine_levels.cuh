@@ -313,14 +313,14 @@ __device__ ABFS_NOINLINE void narrow_to_blocks(const Inst& I, InstCtl* ctl, cons
         __syncthreads();
     }
     uint32_t ent = 0;
-    constexpr uint32_t kChunk = kWarps * kWarpBuf;
-    constexpr uint32_t kItems = kChunk / kThreads;
+    constexpr uint32_t kListChunk = kWarps * kWarpBuf;
+    constexpr uint32_t kItems = kListChunk / kThreads;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t* buf = &sm.wv[0][0];
     unsigned long long eb = 0;
     uint32_t nb = 0;
-    for (uint32_t c0 = 0; c0 < fn; c0 += kChunk, ++nb) {
-        const uint32_t cnt = min(kChunk, fn - c0);
+    for (uint32_t c0 = 0; c0 < fn; c0 += kListChunk, ++nb) {
+        const uint32_t cnt = min(kListChunk, fn - c0);
         for (uint32_t i = tid; i < cnt; i += kThreads) {
             const uint32_t len = ld_l2(I.flen[pn] + c0 + i);
             buf[i] = col_slots(I, mat, ld_l2(I.fbeg[pn] + c0 + i), len);
