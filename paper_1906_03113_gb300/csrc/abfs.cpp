@@ -1193,11 +1193,14 @@ extern "C" int abfs_tune(abfs_graph_t g, const uint32_t* sources, uint32_t count
                 p.ctas_per_sm = cp;
                 cands.push_back(p);
             }
-    // cluster runs of other sizes, and none
+    // cluster runs of other sizes, and none; 16-CTA clusters with one CTA per
+    // SM, so that a run's CTAs sit on 16 SMs (faster on grids and geometric
+    // graphs, whose levels are all cluster runs)
     for (uint32_t cc : {1u, 4u, 16u}) {
         abfs_params p = default_params();
         p.mode = mode;
         p.cluster_ctas = cc;
+        if (cc == 16) p.ctas_per_sm = 1;
         cands.push_back(p);
     }
     if (mode == ABFS_MODE_SUBMATRIX) {
