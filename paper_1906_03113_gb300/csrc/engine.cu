@@ -4,10 +4,11 @@
 // level by level (Algorithm 1, Section 8).  The frontier x_k is kept as a list
 // of vertices in blocks; every vertex carries a weight (the 4-slot chunks that
 // hold its column, each chunk one aligned 16-byte group of row indices), and
-// the level's column entries form one "entry space" of sum(weights) slots.  Work units are ranges of that space, sized per level to
-// about two per CTA, so a unit holds the same number of entries whether it
-// covers one hub column or thousands of short ones (the PRAM "one processor per nonzero" of Theorem 4,
-// with load balance instead of a processor per entry).  Any CTA may take any
+// the level's column entries form one "entry space" of sum(weights) slots.
+// Work units are ranges of that space, sized per level to about two per CTA,
+// so a unit holds the same number of entries whether it covers one hub column
+// or thousands of short ones (the PRAM "one processor per nonzero" of
+// Theorem 4, with load balance instead of a processor per entry).  Any CTA may take any
 // unit of any search; the CTA that completes the last unit of a level advances
 // the search and publishes the next level.  Small levels run on the advancing
 // CTA alone ("narrow" levels), so long, thin searches do not pay a grid-wide
