@@ -101,6 +101,7 @@ MODES += [
                               cluster_edges=1 << 30)),
     ("sub_cluster16_all", dict(mode=SUB, cluster_ctas=16, cluster_min=0, cluster_max=1 << 30,
                                cluster_edges=1 << 30)),
+    ("sub_cluster16_one_per_sm", dict(mode=SUB, cluster_ctas=16, ctas_per_sm=1)),
     ("plain_cluster_all", dict(mode=PLAIN, cluster_min=0, cluster_max=1 << 30,
                                cluster_edges=1 << 30)),
     ("sub_cluster_mixed", dict(mode=SUB, cluster_min=64, cluster_max=300, cluster_edges=3000,
@@ -514,8 +515,9 @@ def test_batch_512_graphs_as_benchmarked():
 def test_grid_4096():
     g = synth.grid_4096()
     G = abfs.graph_create(g.colptr, g.rowidx, directed=False)
+    # the last set is the autotuner's choice for this graph: 16-CTA clusters, one CTA per SM
     for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, cluster_ctas=1),
-               dict(mode=SUB, cluster_ctas=16)):
+               dict(mode=SUB, cluster_ctas=16), dict(mode=SUB, cluster_ctas=16, ctas_per_sm=1)):
         level, parent, st = abfs.run(G, 0, params=_params(**kw), stats=True)
         assert st["status"] == 0 and st["levels"] == 8191
         lev = level.cpu().numpy()
@@ -532,7 +534,8 @@ def test_grid_4096():
 def test_rgg_2_22():
     g = synth.rgg_2_22()
     G = abfs.graph_create(g.colptr, g.rowidx, directed=True)
-    for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, cluster_ctas=1)):
+    for kw in (dict(mode=SUB), dict(mode=PLAIN), dict(mode=SUB, cluster_ctas=1),
+               dict(mode=SUB, cluster_ctas=16, ctas_per_sm=1)):
         level, parent = abfs.run(G, 0, params=_params(**kw))
         _check(g, 0, level, parent, f"rgg22 {kw}")
     G.destroy()
