@@ -700,7 +700,7 @@ def main():
                      "dram_frac": None if dram_gbs is None else dram_gbs / hbm,
                      "dram_from": "ncu dram__bytes of one engine launch / its ncu duration "
                                   "(profiles/), null if the engine changed since",
-                     "kernel": "engine_kernel<0> (one launch per BFS, with 3 small init kernels)",
+                     "kernel": "engine_kernel<0> (one launch per BFS, after one initialisation kernel)",
                      "bytes_per_bfs": float(b_alg.mean()),
                      "bytes_formula": "4*E_adj + 24*n_c",
                      "full_column_gbs": float(b_cols.mean()) / mean_t / 1e9,
@@ -708,7 +708,7 @@ def main():
                             "formula": "nnz_c / load rate + E_adj / red rate",
                             "bound_ms_per_bfs": l2_bound_s * 1e3,
                             "frac": l2_bound_s / mean_t}},
-        "gpu_launches": 4 * nsrc * args.steps,
+        "gpu_launches": 2 * nsrc * args.steps,
         "clocks": clk,
         "per_bfs_ms": float(per_bfs_ms.mean()),
         "reached_mean": float(n_c.mean()), "nnz_c_mean": float(nnz_c.mean()),

@@ -425,6 +425,9 @@ int ensure_workspace(abfs_graph_s* g, const abfs_params& p) {
     w.d_inst = reinterpret_cast<Inst*>(w.base + L.inst);
     Inst I = make_inst(g, w.base, L, 0, nullptr, nullptr);
     cudaError_t e = cudaMemcpy(w.d_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice);
+    // the initialisation kernel of single searches counts its blocks in the
+    // control block, which must start at zero
+    if (e == cudaSuccess) e = cudaMemset(w.base + L.ctl, 0, sizeof(InstCtl));
     if (e != cudaSuccess) {
         free_workspace(w);
         return cuda_fail(e);
@@ -466,8 +469,6 @@ int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* pa
     Workspace& w = g->ws;
     if (g->used) CK(cudaStreamWaitEvent(s, g->last_use, 0));
     const uint32_t bu_ok = (!g->directed && g->sorted && !sigma) ? 1u : 0u;
-    CK(launch_set_query(w.d_inst, source, level, reinterpret_cast<uint32_t*>(parent),
-                        reinterpret_cast<unsigned long long*>(sigma), bu_ok, trace, trace_cap, s));
     EngineArgs a;
     a.insts = w.d_inst;
     a.ninst = 1;
@@ -480,7 +481,9 @@ int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* pa
     a.idle_exit_ns = 0;
     a.p = engine_params(p);
     a.hold_units = test_hold_units();
-    CK(launch_init(a, g->n, s));
+    CK(launch_init_single(a, source, level, reinterpret_cast<uint32_t*>(parent),
+                          reinterpret_cast<unsigned long long*>(sigma), bu_ok, trace, trace_cap,
+                          g->n, s));
     CK(launch_engine(a, grid_size(g, p, 0), s));
     CK(cudaEventRecord(g->last_use, s));
     g->used = true;

@@ -116,6 +116,58 @@ __global__ void init_fill_kernel(const Inst* insts, uint32_t ninst, uint32_t mod
     }
 }
 
+// The control block's start state (zeroed before) for a search whose frontier
+// of level 0 (w0 entry slots) is set up: the first CTA to arrive advances into
+// level 0, which then starts a resident run when it is small (the usual case)
+// instead of a grid phase.  One thread.
+__device__ void start_ctl(const Inst& I, InstCtl* ctl, uint32_t hold_units, unsigned long long w0) {
+    ctl->mat_cur = 0;
+    ctl->mat_prev = 0;
+    ctl->mat_switch = 0;
+    ctl->kind[0] = kPhStart;
+    ctl->plevel[0] = 0;
+    ctl->nitems[0] = 0;
+    ctl->pending[0] = 1 + hold_units;
+    ctl->epoch = 0;
+    ctl->desc[0] = (0ull << 32) | 1ull;
+    ctl->desc[1] = ~0ull;
+    ctl->grab = 0ull;
+    ctl->status = kRunning;
+    if (I.trace && I.trace_cap) {
+        const uint64_t now = globaltimer();
+        I.trace[0] = make_uint4((uint32_t)now, (uint32_t)(now >> 32), (0xFEu << 24), 0u);
+        I.trace[1] = make_uint4(0u, ctl->fcnt[0], (uint32_t)w0, 0u);
+        ctl->trace_n = 1;
+    }
+}
+
+// Level 0 of a single search from source s (outputs cleared before): the
+// source's outputs and visited bit, its frontier block and unit starts, and
+// the control block's start state.  One thread.
+__device__ void start_single(const Inst& I, InstCtl* ctl, const EngineParams& P, uint32_t hold_units,
+                             uint32_t s) {
+    I.level[s] = 0;
+    I.parent[s] = s;
+    if (I.sigma) I.sigma[s] = 1ull;  // x_1 = e_src over the arithmetic semiring
+    if (P.mode == kModeSub) I.bm[0][s >> 5] |= 1u << (s & 31);  // V_2 = V_1 \ {source}
+    // frontier of level 0: one block holding the source
+    const uint32_t len = I.colptr[s + 1] - I.colptr[s];
+    const uint32_t w = col_slots(I, 0, I.colptr[s], len);
+    I.fq[0][0] = s;
+    I.fbeg[0][0] = I.colptr[s];
+    I.fpre[0][0] = 0;
+    I.flen[0][0] = len;
+    I.blk[0][0].vb = 0;
+    I.blk[0][0].nv = 1;
+    I.blk[0][0].eb = 0;
+    for (unsigned long long x = 0; x < w; x += P.unit) I.ustart[0][x / P.unit] = make_uint2(0, 0);
+    ctl->bctr[0] = ((unsigned long long)w << kBlockBits) | 1ull;
+    ctl->fent[0] = len;
+    ctl->fcnt[0] = 1;
+    ctl->reached = 1;
+    start_ctl(I, ctl, hold_units, w);
+}
+
 __global__ void init_source_kernel(EngineArgs a) {
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q == 0) {
@@ -126,7 +178,6 @@ __global__ void init_source_kernel(EngineArgs a) {
     const Inst& I = a.insts[q];
     const EngineParams& P = a.p;
     InstCtl* ctl = I.ctl;
-    unsigned long long w0 = 0;  // entry slots of the frontier of level 0
     if (I.ms) {
         // multi-source search: x_1 = e_src for every source bit; the frontier of
         // level 0 is the distinct sources, one block
@@ -162,49 +213,81 @@ __global__ void init_source_kernel(EngineArgs a) {
         ctl->fent[0] = ent;
         ctl->fcnt[0] = nv;
         ctl->reached = nv;
-        w0 = w;
+        start_ctl(I, ctl, a.hold_units, w);
     } else {
-    const uint32_t s = I.src;
-    I.level[s] = 0;
-    I.parent[s] = s;
-    if (I.sigma) I.sigma[s] = 1ull;  // x_1 = e_src over the arithmetic semiring
-    if (P.mode == kModeSub) I.bm[0][s >> 5] |= 1u << (s & 31);  // V_2 = V_1 \ {source}
-    // frontier of level 0: one block holding the source
-    const uint32_t len = I.colptr[s + 1] - I.colptr[s];
-    const uint32_t w = col_slots(I, 0, I.colptr[s], len);
-    I.fq[0][0] = s;
-    I.fbeg[0][0] = I.colptr[s];
-    I.fpre[0][0] = 0;
-    I.flen[0][0] = len;
-    I.blk[0][0].vb = 0;
-    I.blk[0][0].nv = 1;
-    I.blk[0][0].eb = 0;
-    for (unsigned long long x = 0; x < w; x += P.unit) I.ustart[0][x / P.unit] = make_uint2(0, 0);
-    ctl->bctr[0] = ((unsigned long long)w << kBlockBits) | 1ull;
-    ctl->fent[0] = len;
-    ctl->fcnt[0] = 1;
-    ctl->reached = 1;
-    w0 = w;
+        start_single(I, ctl, P, a.hold_units, I.src);
     }
-    ctl->mat_cur = 0;
-    ctl->mat_prev = 0;
-    ctl->mat_switch = 0;
-    // the first CTA to arrive advances into level 0, which then starts a
-    // resident run when it is small (the usual case) instead of a grid phase
-    ctl->kind[0] = kPhStart;
-    ctl->plevel[0] = 0;
-    ctl->nitems[0] = 0;
-    ctl->pending[0] = 1 + a.hold_units;
-    ctl->epoch = 0;
-    ctl->desc[0] = (0ull << 32) | 1ull;
-    ctl->desc[1] = ~0ull;
-    ctl->grab = 0ull;
-    ctl->status = kRunning;
-    if (I.trace && I.trace_cap) {
-        const uint64_t now = globaltimer();
-        I.trace[0] = make_uint4((uint32_t)now, (uint32_t)(now >> 32), (0xFEu << 24), 0u);
-        I.trace[1] = make_uint4(0u, ctl->fcnt[0], (uint32_t)w0, 0u);
-        ctl->trace_n = 1;
+}
+
+// One search on instance 0 of a workspace (abfs_run and friends): writes the
+// call's fields into the descriptor, clears the outputs and bitmaps (as
+// init_fill_kernel), and the last block to finish sets up the control block
+// and level 0 (as init_source_kernel) -- one launch instead of three.  The
+// last block takes the call's fields from the arguments: its cached view of
+// the descriptor may predate block 0's update.
+__global__ void init_single_kernel(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
+                                   unsigned long long* sigma, uint32_t bu_ok, uint4* trace,
+                                   uint32_t trace_cap, EngineArgs a) {
+    Inst& D = *inst;
+    const uint32_t n = D.n, nwords = D.nwords;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint32_t v = t0; v < n; v += stride) {
+        level[v] = -1;
+        parent[v] = kUnset;
+        if (a.p.mode == kModePlain) D.y[v] = ~0ull;
+        if (sigma) sigma[v] = 0ull;
+    }
+    if (a.p.mode == kModeSub) {
+        // vertices that no column contains start out in both visited bitmaps
+        const uint32_t* inb = D.inb;
+        uint32_t* bm0 = D.bm[0];
+        uint32_t* bm1 = D.bm[1];
+        for (uint32_t w = t0; w < nwords; w += stride) {
+            uint32_t m = 0u;
+            if (inb) {
+                m = ~inb[w];
+                if (w == nwords - 1 && (n & 31)) m &= (1u << (n & 31)) - 1u;
+            }
+            bm0[w] = m;
+            bm1[w] = m;
+        }
+    }
+    InstCtl* ctl = D.ctl;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        D.src = src;
+        D.level = level;
+        D.parent = parent;
+        D.sigma = sigma;
+        D.bu_ok = bu_ok;
+        D.trace = trace;
+        D.trace_cap = trace_cap;
+    }
+    // the last block to get here sees every block's writes
+    __shared__ uint32_t last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicInc(&ctl->init_ticket, gridDim.x - 1) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    uint32_t* c = reinterpret_cast<uint32_t*>(ctl);
+    for (uint32_t w = threadIdx.x; w < sizeof(InstCtl) / 4; w += blockDim.x) c[w] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *a.done_count = 0u;
+        *a.heartbeat = 0ull;
+        Inst I = D;
+        I.src = src;
+        I.level = level;
+        I.parent = parent;
+        I.sigma = sigma;
+        I.bu_ok = bu_ok;
+        I.trace = trace;
+        I.trace_cap = trace_cap;
+        start_single(I, ctl, a.p, a.hold_units, src);
     }
 }
 
@@ -220,6 +303,18 @@ __global__ void set_query_kernel(Inst* inst, uint32_t src, int32_t* level, uint3
     inst->bu_ok = bu_ok;
     inst->trace = trace;
     inst->trace_cap = trace_cap;
+}
+
+cudaError_t launch_init_single(const EngineArgs& a, uint32_t src, int32_t* level, uint32_t* parent,
+                               unsigned long long* sigma, uint32_t bu_ok, uint4* trace,
+                               uint32_t trace_cap, uint32_t n, cudaStream_t s) {
+    uint32_t blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks == 0) blocks = 1;
+    // the descriptor is the workspace's own (writable) copy
+    init_single_kernel<<<blocks, 256, 0, s>>>(const_cast<Inst*>(a.insts), src, level, parent, sigma,
+                                             bu_ok, trace, trace_cap, a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,

@@ -135,6 +135,7 @@ struct InstCtl {
     uint32_t shrink_out;         // shrink: entries written so far
     uint32_t trace_n;            // trace entries written
     uint32_t bu_on;              // hybrid: 1 while levels run bottom-up
+    uint32_t init_ticket;        // blocks of init_single_kernel that are done (wraps to 0)
     unsigned long long entries_read;
     unsigned long long entries_unmasked;
     unsigned long long claims;
@@ -292,6 +293,11 @@ cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t*
                              unsigned long long* sigma, uint32_t bu_ok,
                              uint4* trace, uint32_t trace_cap, cudaStream_t s);
 cudaError_t launch_init(const EngineArgs& a, uint32_t max_n, cudaStream_t s);
+// One search on a workspace's instance 0: the descriptor's per-call fields,
+// the cleared outputs and bitmaps, and level 0, in one launch.
+cudaError_t launch_init_single(const EngineArgs& a, uint32_t src, int32_t* level, uint32_t* parent,
+                               unsigned long long* sigma, uint32_t bu_ok, uint4* trace,
+                               uint32_t trace_cap, uint32_t n, cudaStream_t s);
 cudaError_t launch_engine(const EngineArgs& a, int grid, cudaStream_t s);
 cudaError_t engine_occupancy(uint32_t mode, int* blocks_per_sm);
 // Clusters of `cluster` CTAs of the engine that can be resident at once.
