@@ -145,13 +145,12 @@ __device__ ABFS_NOINLINE void unit_bottom_up(const Inst& I, InstCtl* ctl, const 
 // longer scans run on the whole warp, 32 entries at a time, where each lane
 // keeps the bits no lower lane has (a prefix OR across the warp).
 
-// Outputs of vertex v for the sources in `bits`: level k+1, parent j.
-__device__ __forceinline__ void ms_write(const Inst& I, uint32_t k, uint32_t v, uint32_t j,
-                                         unsigned long long bits) {
+// Parent output of vertex v for the sources in `bits`: j.  (Levels are written
+// source by source for a warp's 32 vertices at once, in unit_ms_update.)
+__device__ __forceinline__ void ms_write(const Inst& I, uint32_t v, uint32_t j, unsigned long long bits) {
     while (bits) {
         const uint32_t s = (uint32_t)(__ffsll((long long)bits) - 1);
         bits &= bits - 1;
-        I.ms_level[s][v] = (int32_t)(k + 1);
         I.ms_parent[s][v] = (int32_t)j;
     }
 }
@@ -206,7 +205,7 @@ __device__ ABFS_NOINLINE void unit_ms_update(const Inst& I, InstCtl* ctl, const 
                 for (int x = 0; x < 4; ++x) {
                     const unsigned long long hit = fm[x] & rem;
                     if (hit) {
-                        ms_write(I, k, v, jj[x], hit);
+                        ms_write(I, v, jj[x], hit);
                         rem &= ~hit;
                     }
                 }
@@ -228,11 +227,23 @@ __device__ ABFS_NOINLINE void unit_ms_update(const Inst& I, InstCtl* ctl, const 
                     // the bits this lane's entry is the first (least) to hold
                     const unsigned long long prev = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
                     const unsigned long long first = lane ? (h & ~prev) : h;
-                    if (first) ms_write(I, k, lv, j, first);
+                    if (first) ms_write(I, lv, j, first);
                     if (lane == 0) t.read += min(32u, lend - x);
                     lrem &= ~__shfl_sync(0xFFFFFFFFu, incl, 31);
                 }
                 if (lane == ldr) defer = false;
+            }
+            {
+                // levels source by source: the lanes that hold a source's bit
+                // write consecutive vertices of that source's level array
+                unsigned long long un = nb;
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) un |= __shfl_xor_sync(0xFFFFFFFFu, un, d);
+                while (un) {
+                    const uint32_t s = (uint32_t)(__ffsll((long long)un) - 1);
+                    un &= un - 1;
+                    if ((nb >> s) & 1ull) I.ms_level[s][v] = (int32_t)(k + 1);
+                }
             }
             stage_warp(nb != 0ull, v, sm, wc);
             if (wc > (uint32_t)(kWarpBuf - 32)) warp_flush(sm, I, ctl, P, pn, 0u, wc);
