@@ -148,6 +148,9 @@ def test_bounded_wait_runs_out_with_timeout_status(lib):
         # a batch of three: every search times out, the launch returns
         _, _, st = abfs.run_batch([G] * 3, [s, 0, 1], params=p)
         assert st == [binding.ERR_TIMEOUT] * 3
+        # many searches into host memory: each search's own status comes back
+        _, _, st = abfs.run_host_many(G, [s, 0, 1], params=p)
+        assert st == [binding.ERR_TIMEOUT] * 3
     finally:
         assert lib.abfs_test_hold_first_phase(0) == 0
     torch.cuda.synchronize()
