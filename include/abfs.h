@@ -179,6 +179,27 @@ int abfs_graph_destroy(abfs_graph_t g);
 /* n, nnz and the directed flag of a graph (any pointer may be NULL). */
 int abfs_graph_info(abfs_graph_t g, uint32_t* n, uint64_t* nnz, int* directed);
 
+/*
+ * Adds to the graph a copy whose vertices are renumbered by column-length
+ * class (a layout choice; the paper's method is unchanged): first the longest
+ * columns, whole length groups of at most n/64 vertices; then the next
+ * longest, up to n/8 with the first class; then the other non-empty columns;
+ * the empty ones last; input order inside each class.  On graphs with a
+ * skewed degree distribution the mask tests and claims of the high-degree
+ * rows then fall on few cache lines.  Graphs whose input order carries
+ * locality (grids, geometric graphs) gain nothing from it.  Single searches in submatrix mode
+ * without path counts (abfs_run, abfs_run_host, abfs_run_host_many,
+ * abfs_run_trace, and the autotuner's trials) run on the copy; a last pass
+ * writes level[] and parent[] in the input's labels, with the same least-index
+ * parents (Theorem 1).  Path counts, the hybrid's bottom-up levels, the
+ * comparator, batches, serving and abfs_run_static keep the input numbering.
+ * Costs a second copy of colptr/rowidx plus 8n bytes of label maps, and 8n
+ * bytes more per workspace.  Builds on the host (the CSC is copied out and
+ * back); synchronises; calling it again does nothing.  Returns ABFS_ERR_OOM or
+ * ABFS_ERR_CUDA on failure, leaving the graph as it was.
+ */
+int abfs_graph_relabel(abfs_graph_t g);
+
 /* Device bytes one search on this graph needs beyond the graph itself
  * (bitmaps, frontier queues, control), for the given parameters
  * (NULL = defaults).  Serving admission uses this figure. */

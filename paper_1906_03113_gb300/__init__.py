@@ -27,6 +27,7 @@ from .binding import (  # noqa: F401
     run_batch,
     run_host,
     run_host_many,
+    graph_relabel,
     run_trace,
     strerror,
     tune,

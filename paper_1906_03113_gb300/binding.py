@@ -157,6 +157,7 @@ def load():
         "abfs_run_counts": ([vp, u32, vp, vp, vp, vp, P(Params), P(Stats)], c_int),
         "abfs_calibrate": ([u32, P(Calibration), vp], c_int),
         "abfs_run_host": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
+        "abfs_graph_relabel": ([vp], c_int),
         "abfs_run_host_many": ([vp, P(u32), u32, vp, vp, vp, P(Params), P(i32)], c_int),
         "abfs_run_trace": ([vp, u32, vp, vp, vp, P(Params), vp, u32, P(u32)], c_int),
         "abfs_run_batch": ([P(vp), P(u32), u32, P(vp), P(vp), vp, P(Params), P(i32)], c_int),
@@ -389,6 +390,12 @@ def run_host(g: Graph, source: int, level_host: np.ndarray | None = None,
                               ctypes.byref(st) if st else None)
     _check(rc, "abfs_run_host")
     return (level_host, parent_host, st.as_dict()) if stats else (level_host, parent_host)
+
+
+def graph_relabel(g: Graph) -> None:
+    """abfs_graph_relabel: single searches on g run on a copy numbered by
+    column-length class; outputs stay in g's labels."""
+    _check(load().abfs_graph_relabel(g.handle), "abfs_graph_relabel")
 
 
 def run_host_many(g: Graph, sources, level_host=None, parent_host=None, stream=None,

@@ -199,7 +199,7 @@ bool same_layout(const abfs_params& a, const abfs_params& b) {
 // per-search workspace layout
 // ---------------------------------------------------------------------------
 
-Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p, uint32_t ms) {
+Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p, uint32_t ms, bool relabel) {
     Layout L;
     std::memset(&L, 0, sizeof(L));
     const size_t A = 256;
@@ -251,6 +251,13 @@ Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p, uint32_t ms) {
             L.slen[i] = take((size_t)n * 4);
             L.srows[i] = take((size_t)std::max<uint64_t>(nnz, 1) * 4);
         }
+    }
+    if (relabel && !ms) {
+        // searches on the relabelled copy: a second descriptor and the
+        // internal outputs
+        L.inst_r = take(sizeof(Inst));
+        L.lev_i = take((size_t)n * 4);
+        L.par_i = take((size_t)n * 4);
     }
     L.total = o;
     return L;
@@ -319,7 +326,9 @@ struct Workspace {
     char* base = nullptr;
     Layout L{};
     abfs_params p{};
+    bool relabel = false;     // laid out for searches on the relabelled copy too
     Inst* d_inst = nullptr;   // device descriptor (instance 0)
+    Inst* d_inst_r = nullptr; // the same on the relabelled copy
     uint32_t* d_done = nullptr;
     unsigned long long* d_beat = nullptr;
     InstCtl* h_ctl = nullptr; // pinned copy for stats
@@ -332,6 +341,17 @@ struct abfs_graph_s {
     uint64_t nnz = 0;
     int directed = 0;
     bool sorted = false;          // every column's row indices ascend (bottom-up levels allowed)
+    // abfs_graph_relabel: a copy with vertices numbered by column-length class
+    // (internal labels) and the maps between the two numberings
+    bool relabeled = false;
+    uint32_t* r_colptr = nullptr;
+    uint32_t* r_rowidx = nullptr;
+    uint32_t* r_inb = nullptr;
+    uint32_t* d_lab = nullptr;     // internal label -> input label
+    uint32_t* d_pos = nullptr;     // input label -> internal label
+    std::vector<uint32_t> h_pos;
+    uint32_t r_keep = 0;           // internal vertices that may be reached (all but the
+                                   // empty columns of an undirected graph)
     uint32_t* d_inb = nullptr;    // rows that occur in some column, one bit per vertex
     int device = 0;
     int sms = 0;
@@ -398,7 +418,7 @@ Inst make_inst(const abfs_graph_s* g, char* base, const Layout& L, uint32_t src,
 // Ensures g->ws fits params p (reallocating after the previous use finished).
 int ensure_workspace(abfs_graph_s* g, const abfs_params& p) {
     Workspace& w = g->ws;
-    if (w.base && same_layout(w.p, p)) {
+    if (w.base && same_layout(w.p, p) && w.relabel == g->relabeled) {
         w.p = p;
         return ABFS_OK;
     }
@@ -406,7 +426,7 @@ int ensure_workspace(abfs_graph_s* g, const abfs_params& p) {
         if (g->used) CK(cudaEventSynchronize(g->last_use));
         free_workspace(w);
     }
-    Layout L = layout_for(g->n, g->nnz, p);
+    Layout L = layout_for(g->n, g->nnz, p, 0, g->relabeled);
     int rc = dev_alloc((void**)&w.base, L.total);
     if (rc) return rc;
     rc = dev_alloc((void**)&w.d_done, 64);
@@ -425,6 +445,16 @@ int ensure_workspace(abfs_graph_s* g, const abfs_params& p) {
     w.d_inst = reinterpret_cast<Inst*>(w.base + L.inst);
     Inst I = make_inst(g, w.base, L, 0, nullptr, nullptr);
     cudaError_t e = cudaMemcpy(w.d_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice);
+    w.relabel = g->relabeled;
+    w.d_inst_r = nullptr;
+    if (e == cudaSuccess && g->relabeled) {
+        Inst Ir = make_inst_raw(g->r_colptr, g->r_rowidx, g->n, w.base, L, 0, nullptr, nullptr);
+        Ir.inb = g->r_inb;
+        Ir.bu_ok = 0;  // the relabelled columns are not in ascending input-label order
+        Ir.lab = g->d_lab;
+        w.d_inst_r = reinterpret_cast<Inst*>(w.base + L.inst_r);
+        e = cudaMemcpy(w.d_inst_r, &Ir, sizeof(Inst), cudaMemcpyHostToDevice);
+    }
     // the initialisation kernel of single searches counts its blocks in the
     // control block, which must start at zero
     if (e == cudaSuccess) e = cudaMemset(w.base + L.ctl, 0, sizeof(InstCtl));
@@ -468,9 +498,11 @@ int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* pa
     if (rc) return rc;
     Workspace& w = g->ws;
     if (g->used) CK(cudaStreamWaitEvent(s, g->last_use, 0));
-    const uint32_t bu_ok = (!g->directed && g->sorted && !sigma) ? 1u : 0u;
+    // submatrix searches without path counts run on the relabelled copy
+    const bool rel = w.relabel && p.mode == ABFS_MODE_SUBMATRIX && !sigma;
+    const uint32_t bu_ok = (!rel && !g->directed && g->sorted && !sigma) ? 1u : 0u;
     EngineArgs a;
-    a.insts = w.d_inst;
+    a.insts = rel ? w.d_inst_r : w.d_inst;
     a.ninst = 1;
     a.done_count = w.d_done;
     a.heartbeat = w.d_beat;
@@ -481,7 +513,19 @@ int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* pa
     a.idle_exit_ns = 0;
     a.p = engine_params(p);
     a.hold_units = test_hold_units();
-    CK(launch_init_single(a, source, level, reinterpret_cast<uint32_t*>(parent),
+    if (rel) {
+        int32_t* lev_i = reinterpret_cast<int32_t*>(w.base + w.L.lev_i);
+        uint32_t* par_i = reinterpret_cast<uint32_t*>(w.base + w.L.par_i);
+        CK(launch_init_single(a, g->h_pos[source], source, lev_i, par_i, nullptr, 0u, trace,
+                              trace_cap, g->n, s));
+        CK(launch_engine(a, grid_size(g, p, 0), s));
+        CK(launch_relabel_out(g->d_pos, lev_i, par_i, level, parent, g->n, g->r_keep,
+                              g->h_pos[source], s));
+        CK(cudaEventRecord(g->last_use, s));
+        g->used = true;
+        return ABFS_OK;
+    }
+    CK(launch_init_single(a, source, source, level, reinterpret_cast<uint32_t*>(parent),
                           reinterpret_cast<unsigned long long*>(sigma), bu_ok, trace, trace_cap,
                           g->n, s));
     CK(launch_engine(a, grid_size(g, p, 0), s));
@@ -604,8 +648,102 @@ extern "C" int abfs_graph_destroy(abfs_graph_t g) {
     dev_free(g->d_colptr);
     dev_free(g->d_rowidx);
     dev_free(g->d_inb);
+    dev_free(g->r_colptr);
+    dev_free(g->r_rowidx);
+    dev_free(g->r_inb);
+    dev_free(g->d_lab);
+    dev_free(g->d_pos);
     if (g->last_use) cudaEventDestroy(g->last_use);
     delete g;
+    return ABFS_OK;
+}
+
+extern "C" int abfs_graph_relabel(abfs_graph_t g) {
+    if (!g) return ABFS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->relabeled) return ABFS_OK;
+    if (g->used) CK(cudaEventSynchronize(g->last_use));
+    const uint32_t n = g->n;
+    const uint64_t nnz = g->nnz;
+    std::vector<uint32_t> cp((size_t)n + 1), rows(std::max<uint64_t>(nnz, 1));
+    CK(cudaMemcpy(cp.data(), g->d_colptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost));
+    if (nnz) CK(cudaMemcpy(rows.data(), g->d_rowidx, nnz * 4, cudaMemcpyDeviceToHost));
+    // internal label of each vertex: by class, and in input order inside a
+    // class -- (0) the longest columns, whole length groups of at most n/64
+    // vertices in all; (1) the next longest, up to n/8 with class 0; (2) the
+    // other non-empty columns; (3) the empty ones.  The hubs the first levels
+    // reach share cache lines of every per-vertex array; the input order
+    // inside a class keeps whatever locality the input numbering had.
+    uint32_t maxdeg = 0;
+    for (uint32_t v = 0; v < n; ++v) maxdeg = std::max(maxdeg, cp[v + 1] - cp[v]);
+    std::vector<uint64_t> hist((size_t)maxdeg + 1, 0);
+    for (uint32_t v = 0; v < n; ++v) ++hist[cp[v + 1] - cp[v]];
+    // thr[c]: the shortest length in classes 0..c (length groups kept whole)
+    uint32_t thr[2];
+    {
+        const uint64_t cap[2] = {(uint64_t)n / 64, (uint64_t)n / 8};
+        uint64_t acc = 0;
+        uint32_t t = maxdeg + 1;
+        for (int c = 0; c < 2; ++c) {
+            while (t > 1 && acc + hist[t - 1] <= cap[c]) acc += hist[--t];
+            thr[c] = t;
+        }
+    }
+    std::vector<uint8_t> cls(n);
+    uint64_t start[5] = {0, 0, 0, 0, 0};
+    for (uint32_t v = 0; v < n; ++v) {
+        const uint32_t d = cp[v + 1] - cp[v];
+        cls[v] = d >= thr[0] ? 0 : (d >= thr[1] ? 1 : (d > 0 ? 2 : 3));
+        ++start[cls[v] + 1];
+    }
+    for (int c = 1; c < 5; ++c) start[c] += start[c - 1];
+    std::vector<uint32_t> lab(n), pos(n);
+    for (uint32_t v = 0; v < n; ++v) {
+        const uint32_t i = (uint32_t)start[cls[v]]++;
+        lab[i] = v;
+        pos[v] = i;
+    }
+    // the relabelled CSC: column i is column lab[i], its rows renamed
+    std::vector<uint32_t> rcp((size_t)n + 1), rrows(std::max<uint64_t>(nnz, 1));
+    rcp[0] = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint32_t v = lab[i], b = cp[v], len = cp[v + 1] - b;
+        for (uint32_t x = 0; x < len; ++x) rrows[(size_t)rcp[i] + x] = pos[rows[(size_t)b + x]];
+        rcp[i + 1] = rcp[i] + len;
+    }
+    const uint32_t nwords = (n + 31) / 32;
+    int rc = dev_alloc((void**)&g->r_colptr, ((size_t)n + 1) * 4);
+    if (!rc) rc = dev_alloc((void**)&g->r_rowidx, std::max<uint64_t>(nnz, 1) * 4);
+    if (!rc) rc = dev_alloc((void**)&g->r_inb, (size_t)nwords * 4);
+    if (!rc) rc = dev_alloc((void**)&g->d_lab, (size_t)n * 4);
+    if (!rc) rc = dev_alloc((void**)&g->d_pos, (size_t)n * 4);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        e = cudaMemcpy(g->r_colptr, rcp.data(), ((size_t)n + 1) * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && nnz)
+            e = cudaMemcpy(g->r_rowidx, rrows.data(), nnz * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_lab, lab.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_pos, pos.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_row_bitmap(g->r_rowidx, nnz, g->r_inb, nwords, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (rc || e != cudaSuccess) {
+        for (uint32_t** q : {&g->r_colptr, &g->r_rowidx, &g->r_inb, &g->d_lab, &g->d_pos}) {
+            dev_free(*q);
+            *q = nullptr;
+        }
+        return rc ? rc : cuda_fail(e);
+    }
+    // an undirected graph's empty columns (the last internal labels) are
+    // vertices without edges: unreachable from any other source
+    uint32_t keep = n;
+    if (!g->directed)
+        while (keep > 0 && rcp[keep] == rcp[keep - 1]) --keep;
+    g->h_pos = std::move(pos);
+    g->r_keep = keep;
+    g->relabeled = true;
+    // the next search lays its workspace out for the relabelled copy
+    free_workspace(g->ws);
     return ABFS_OK;
 }
 
@@ -623,7 +761,7 @@ extern "C" int abfs_graph_footprint(abfs_graph_t g, const abfs_params* params, s
     const abfs_params& p = pick_params(g, params, tmp);
     int rc = check_params(p);
     if (rc) return rc;
-    *bytes = layout_for(g->n, g->nnz, p).total;
+    *bytes = layout_for(g->n, g->nnz, p, 0, g->relabeled).total;
     return ABFS_OK;
 }
 

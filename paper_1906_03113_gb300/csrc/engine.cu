@@ -141,13 +141,13 @@ __device__ void start_ctl(const Inst& I, InstCtl* ctl, uint32_t hold_units, unsi
     }
 }
 
-// Level 0 of a single search from source s (outputs cleared before): the
-// source's outputs and visited bit, its frontier block and unit starts, and
-// the control block's start state.  One thread.
+// Level 0 of a single search from source s, input label s_label (outputs
+// cleared before): the source's outputs and visited bit, its frontier block
+// and unit starts, and the control block's start state.  One thread.
 __device__ void start_single(const Inst& I, InstCtl* ctl, const EngineParams& P, uint32_t hold_units,
-                             uint32_t s) {
+                             uint32_t s, uint32_t s_label) {
     I.level[s] = 0;
-    I.parent[s] = s;
+    I.parent[s] = s_label;
     if (I.sigma) I.sigma[s] = 1ull;  // x_1 = e_src over the arithmetic semiring
     if (P.mode == kModeSub) I.bm[0][s >> 5] |= 1u << (s & 31);  // V_2 = V_1 \ {source}
     // frontier of level 0: one block holding the source
@@ -215,7 +215,7 @@ __global__ void init_source_kernel(EngineArgs a) {
         ctl->reached = nv;
         start_ctl(I, ctl, a.hold_units, w);
     } else {
-        start_single(I, ctl, P, a.hold_units, I.src);
+        start_single(I, ctl, P, a.hold_units, I.src, I.lab ? I.lab[I.src] : I.src);
     }
 }
 
@@ -225,9 +225,9 @@ __global__ void init_source_kernel(EngineArgs a) {
 // and level 0 (as init_source_kernel) -- one launch instead of three.  The
 // last block takes the call's fields from the arguments: its cached view of
 // the descriptor may predate block 0's update.
-__global__ void init_single_kernel(Inst* inst, uint32_t src, int32_t* level, uint32_t* parent,
-                                   unsigned long long* sigma, uint32_t bu_ok, uint4* trace,
-                                   uint32_t trace_cap, EngineArgs a) {
+__global__ void init_single_kernel(Inst* inst, uint32_t src, uint32_t src_label, int32_t* level,
+                                   uint32_t* parent, unsigned long long* sigma, uint32_t bu_ok,
+                                   uint4* trace, uint32_t trace_cap, EngineArgs a) {
     Inst& D = *inst;
     const uint32_t n = D.n, nwords = D.nwords;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -287,7 +287,7 @@ __global__ void init_single_kernel(Inst* inst, uint32_t src, int32_t* level, uin
         I.bu_ok = bu_ok;
         I.trace = trace;
         I.trace_cap = trace_cap;
-        start_single(I, ctl, a.p, a.hold_units, src);
+        start_single(I, ctl, a.p, a.hold_units, src, src_label);
     }
 }
 
@@ -305,15 +305,47 @@ __global__ void set_query_kernel(Inst* inst, uint32_t src, int32_t* level, uint3
     inst->trace_cap = trace_cap;
 }
 
-cudaError_t launch_init_single(const EngineArgs& a, uint32_t src, int32_t* level, uint32_t* parent,
-                               unsigned long long* sigma, uint32_t bu_ok, uint4* trace,
-                               uint32_t trace_cap, uint32_t n, cudaStream_t s) {
+cudaError_t launch_init_single(const EngineArgs& a, uint32_t src, uint32_t src_label, int32_t* level,
+                               uint32_t* parent, unsigned long long* sigma, uint32_t bu_ok,
+                               uint4* trace, uint32_t trace_cap, uint32_t n, cudaStream_t s) {
     uint32_t blocks = (n + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     if (blocks == 0) blocks = 1;
     // the descriptor is the workspace's own (writable) copy
-    init_single_kernel<<<blocks, 256, 0, s>>>(const_cast<Inst*>(a.insts), src, level, parent, sigma,
-                                             bu_ok, trace, trace_cap, a);
+    init_single_kernel<<<blocks, 256, 0, s>>>(const_cast<Inst*>(a.insts), src, src_label, level,
+                                             parent, sigma, bu_ok, trace, trace_cap, a);
+    return cudaGetLastError();
+}
+
+// A search on a relabelled graph ran on internal outputs: the caller's level[o]
+// and parent[o] are those of internal vertex pos[o] (parents already hold
+// input labels).  Internal vertices from n_keep on other than the source s_i
+// are known to be unreached (columns without entries of an undirected graph)
+// and are not looked up.  Reads pos in order and the internal outputs where
+// it points.
+__global__ void relabel_out_kernel(const uint32_t* __restrict__ pos, const int32_t* __restrict__ lev_i,
+                                   const uint32_t* __restrict__ par_i, int32_t* level, int32_t* parent,
+                                   uint32_t n, uint32_t n_keep, uint32_t s_i) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += stride) {
+        const uint32_t i = pos[o];
+        int32_t lv = -1, pr = -1;
+        if (i < n_keep || i == s_i) {
+            lv = __ldg(lev_i + i);
+            pr = (int32_t)__ldg(par_i + i);
+        }
+        level[o] = lv;
+        parent[o] = pr;
+    }
+}
+
+cudaError_t launch_relabel_out(const uint32_t* pos, const int32_t* lev_i, const uint32_t* par_i,
+                               int32_t* level, int32_t* parent, uint32_t n, uint32_t n_keep,
+                               uint32_t s_i, cudaStream_t s) {
+    uint32_t blocks = (n + 255) / 256;
+    if (blocks > 2048) blocks = 2048;
+    if (blocks == 0) blocks = 1;
+    relabel_out_kernel<<<blocks, 256, 0, s>>>(pos, lev_i, par_i, level, parent, n, n_keep, s_i);
     return cudaGetLastError();
 }
 

@@ -208,8 +208,9 @@ struct ClusterBox {
 };
 
 struct Smem {
-    // staged frontier vertices of the unit being expanded: id, column begin
-    // minus slot offset (row index of slot s is b[t] + s), slot offset, and
+    // staged frontier vertices of the unit being expanded: the column index
+    // their products carry (the vertex, or its input label on a relabelled
+    // graph), column begin minus slot offset (row index of slot s is b[t] + s), slot offset, and
     // end of the vertex's entry slots
     uint32_t v[kTileMax + 1];
     uint32_t b[kTileMax + 1];

@@ -459,6 +459,9 @@ __device__ ABFS_NOINLINE void unit_level(const Inst& I, InstCtl* ctl, const Engi
         }
         const uint32_t cnt = sm.sub_cnt, nseg = sm.sub_nseg;
         const unsigned long long g0 = sm.sub_g0;
+        // slots [lo, hi) of this sub-tile belong to the unit
+        const uint32_t lo = (uint32_t)(e - g0);
+        const uint32_t hi_s = (uint32_t)(min(u_hi, (unsigned long long)sm.sub_end) - g0);
         for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
             uint32_t q = 0, hi = nseg;  // seg_pos[q] <= s < seg_pos[hi]
             while (hi - q > 1) {
@@ -467,32 +470,34 @@ __device__ ABFS_NOINLINE void unit_level(const Inst& I, InstCtl* ctl, const Engi
                 else hi = mid;
             }
             const uint32_t idx = sm.seg_idx[q] + (s - sm.seg_pos[q]);
-            sm.v[s] = ld_l2(I.fq[p] + idx);
+            const uint32_t v = ld_l2(I.fq[p] + idx);
+            const uint32_t len = ld_l2(I.flen[p] + idx);
+            const uint32_t st = (uint32_t)(sm.seg_eb[q] + ld_l2(I.fpre[p] + idx) - g0);
+            // the column index its products carry: the input label on a relabelled graph
+            sm.v[s] = I.lab ? ld_ro(I.lab + v) : v;
             sm.b[s] = ld_l2(I.fbeg[p] + idx);
-            sm.end[s] = ld_l2(I.flen[p] + idx);
-            sm.off[s] = (uint32_t)(sm.seg_eb[q] + ld_l2(I.fpre[p] + idx) - g0);
+            sm.end[s] = len;
+            sm.off[s] = st;
+            if (st >= lo && st < hi_s) {
+                // the vertex's first slot lies in this unit: it joins the visited
+                // set of the next level's test (once)
+                if (MODE == kModeSub && VAR != kVarMs) atomicOr(I.bm[p ^ 1] + (v >> 5), 1u << (v & 31));
+                nnz_local += (mat == 0) ? len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
+            }
         }
         if (threadIdx.x == 0) sm.off[cnt] = (uint32_t)(sm.sub_end - g0);
         if (threadIdx.x < (uint32_t)kWarps) sm.wvb[threadIdx.x] = kNoVb;
-        // slots [lo, hi) of this sub-tile belong to the unit
-        const uint32_t lo = (uint32_t)(e - g0);
-        const uint32_t hi_s = (uint32_t)(min(u_hi, (unsigned long long)sm.sub_end) - g0);
         const uint32_t nwords = ((hi_s - lo) / kChunk + 31) / 32 + 1;
         for (uint32_t w = threadIdx.x; w < nwords; w += kThreads) sm.sbits[w] = 0u;
         __syncthreads();
         for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
             const uint32_t st = sm.off[s];
-            const uint32_t len = sm.end[s];
             set_slot_map(sm, I, mat, s, st);
             mark_warp_starts(sm, s, st / kChunk, sm.off[s + 1] / kChunk, lo / kChunk, hi_s / kChunk);
             if (st >= lo && st < hi_s) {
-                // the vertex's first slot lies in this unit: it joins the visited
-                // set of the next level's test (once), and starts a run of chunks
+                // the vertex's first slot lies in this unit: it starts a run of chunks
                 const uint32_t c = (st - lo) / kChunk;
                 atomicOr(&sm.sbits[c >> 5], 1u << (c & 31));
-                const uint32_t v = sm.v[s];
-                if (MODE == kModeSub && VAR != kVarMs) atomicOr(I.bm[p ^ 1] + (v >> 5), 1u << (v & 31));
-                nnz_local += (mat == 0) ? len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
             }
         }
         __syncthreads();

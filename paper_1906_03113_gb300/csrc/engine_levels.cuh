@@ -103,7 +103,7 @@ __device__ __forceinline__ void narrow_expand(const Inst& I, InstCtl* ctl, const
                 beg = c.beg;
                 len = c.len;
             }
-            sm.v[s] = v;
+            sm.v[s] = I.lab ? ld_ro(I.lab + v) : v;  // the column index of its products
             sm.b[s] = beg;
             sm.end[s] = len;
             sm.off[s] = col_slots(I, mat, beg, len);
@@ -174,7 +174,7 @@ __device__ ABFS_NOINLINE bool narrow_expand_short(const Inst& I, InstCtl* ctl, c
     const uint32_t p = k & 1, pn = p ^ 1;
     const uint32_t tid = threadIdx.x, lane = tid & 31;
     const bool have = tid < f;
-    uint32_t v = 0, beg = 0, len = 0;
+    uint32_t v = 0, vo = 0, beg = 0, len = 0;  // vo: the claims' column index (v's input label)
     if (have) {
         const uint32_t at = base + tid;
         v = ld_l2(I.fq[p] + at);
@@ -195,6 +195,7 @@ __device__ ABFS_NOINLINE bool narrow_expand_short(const Inst& I, InstCtl* ctl, c
     for (uint32_t j = 0; j < kShortCol; ++j)
         r[j] = (have && j < len) ? ld_row(rows, beg + j, mat, pol) : kUnset;
     if (have) {
+        vo = I.lab ? ld_ro(I.lab + v) : v;  // issued beside the row loads
         // the frontier joins the visited set of the next level's test
         if (MODE == kModeSub) atomicOr(I.bm[pn] + (v >> 5), 1u << (v & 31));
         nnz_local += (mat == 0) ? len : (ld_ro(I.colptr + v + 1) - ld_ro(I.colptr + v));
@@ -219,7 +220,7 @@ __device__ ABFS_NOINLINE bool narrow_expand_short(const Inst& I, InstCtl* ctl, c
             if (!((w[j] >> (r[j] & 31)) & 1u)) {
                 ++t.unmasked;
                 ++t.claims;
-                old[j] = atomicMin(I.parent + r[j], v);
+                old[j] = atomicMin(I.parent + r[j], vo);
                 const ColRef c = col_of(I, mat_next, r[j]);
                 nb[j] = c.beg;
                 nl[j] = c.len;

@@ -166,6 +166,10 @@ struct Inst {
     uint32_t* fbeg[2];       // their column begins (kUnset: no entries)
     uint32_t* fpre[2];       // their entry offsets within their block
     uint32_t* flen[2];       // their column lengths
+    // relabelled graph (vertices numbered by column-length class): the input
+    // label of each vertex, looked up where a frontier vertex is staged
+    // (nullptr: the labels are the input's).  Parents are always input labels.
+    const uint32_t* lab;
     Block* blk[2];           // frontier blocks
     uint2* ustart[2];        // unit u starts in (block, vertex index in block)
     unsigned long long* y;   // comparator: stamped (min, index) accumulator
@@ -261,8 +265,9 @@ enum ProfSlot : int {
 struct Layout {
     uint64_t nnz;
     size_t bm[2], fbm[2], fq[2], fbeg[2], fpre[2], flen[2], blk[2], ustart[2], y, touched, sbeg[2], slen[2],
-        srows[2], ctl, inst;
+        srows[2], ctl, inst, inst_r;
     size_t ms_vis, ms_fr[2], ms_nx, ms_src, ms_lev, ms_par;  // multi-source searches only
+    size_t lev_i, par_i;  // searches on a relabelled graph: internal outputs
     size_t total;
     uint32_t nwords, bcap, ncopies;
     unsigned long long ucap, scap;
@@ -273,7 +278,8 @@ abfs_params default_params();
 bool shrink_enabled(const abfs_params& p);
 int check_params(const abfs_params& p);
 EngineParams engine_params(const abfs_params& p);
-Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p, uint32_t ms = 0);
+Layout layout_for(uint32_t n, uint64_t nnz, const abfs_params& p, uint32_t ms = 0,
+                  bool relabel = false);
 Inst make_inst_raw(const uint32_t* colptr, const uint32_t* rowidx, uint32_t n, char* base,
                    const Layout& L, uint32_t src, int32_t* level, int32_t* parent);
 int grid_for(int sms, const abfs_params& p);
@@ -295,9 +301,15 @@ cudaError_t launch_set_query(Inst* inst, uint32_t src, int32_t* level, uint32_t*
 cudaError_t launch_init(const EngineArgs& a, uint32_t max_n, cudaStream_t s);
 // One search on a workspace's instance 0: the descriptor's per-call fields,
 // the cleared outputs and bitmaps, and level 0, in one launch.
-cudaError_t launch_init_single(const EngineArgs& a, uint32_t src, int32_t* level, uint32_t* parent,
-                               unsigned long long* sigma, uint32_t bu_ok, uint4* trace,
-                               uint32_t trace_cap, uint32_t n, cudaStream_t s);
+cudaError_t launch_init_single(const EngineArgs& a, uint32_t src, uint32_t src_label, int32_t* level,
+                               uint32_t* parent, unsigned long long* sigma, uint32_t bu_ok,
+                               uint4* trace, uint32_t trace_cap, uint32_t n, cudaStream_t s);
+// A search on a relabelled graph: the caller's outputs in input labels,
+// level[o] = lev_i[pos[o]], parent[o] = par_i[pos[o]] (-1 without a look-up for
+// internal vertices >= n_keep other than the source s_i).
+cudaError_t launch_relabel_out(const uint32_t* pos, const int32_t* lev_i, const uint32_t* par_i,
+                               int32_t* level, int32_t* parent, uint32_t n, uint32_t n_keep,
+                               uint32_t s_i, cudaStream_t s);
 cudaError_t launch_engine(const EngineArgs& a, int grid, cudaStream_t s);
 cudaError_t engine_occupancy(uint32_t mode, int* blocks_per_sm);
 // Clusters of `cluster` CTAs of the engine that can be resident at once.

@@ -61,6 +61,7 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     assert lib.abfs_run(None, 0, None, None, None, None, None) == binding.ERR_INVALID_ARG
     assert lib.abfs_run_counts(None, 0, None, None, None, None, None, None) == binding.ERR_INVALID_ARG
     assert lib.abfs_run_host_many(None, None, 0, None, None, None, None, None) == binding.ERR_INVALID_ARG
+    assert lib.abfs_graph_relabel(None) == binding.ERR_INVALID_ARG
     assert lib.abfs_batch_create_counts(None, None, 0, None, None, None, None, None,
                                         None) == binding.ERR_INVALID_ARG
     cal = binding.Calibration()

@@ -219,6 +219,44 @@ def test_run_host_matches(small):
     _check(g, s, lev_h, par_h, "run_host")
 
 
+RELABEL = ["rmat_14", "er_2000", "grid_100x37", "rgg_2_15", "star", "path_3000", "no_edges"]
+
+
+@pytest.mark.parametrize("name", RELABEL)
+def test_relabelled_graph_all_modes(small, name):
+    """A graph relabelled by descending column length (abfs_graph_relabel): every
+    mode equals the oracle in the input's labels -- the submatrix searches run
+    on the copy (wide, reduction, resident, cluster and shrink paths), the
+    comparator, the hybrid and path counts keep the input numbering."""
+    gs, _ = small
+    g = gs[name]
+    G = abfs.graph_create(g.colptr, g.rowidx, directed=g.directed)
+    abfs.graph_relabel(G)
+    abfs.graph_relabel(G)  # a second call changes nothing
+    for mode_name, kw in MODES:
+        p = _params(**kw)
+        for s in _sources(g):
+            level, parent, st = abfs.run(G, s, params=p, stats=True)
+            assert st["status"] == 0, (name, mode_name, s)
+            _check(g, s, level, parent, f"relabelled {name} {mode_name} src{s}")
+    s = _sources(g)[-1]
+    lev_h, par_h = abfs.run_host(G, s)
+    _check(g, s, lev_h, par_h, f"relabelled {name} run_host")
+    lev, par, st = abfs.run_host_many(G, _sources(g))
+    assert st == [0] * len(_sources(g))
+    for i, s in enumerate(_sources(g)):
+        _check(g, s, lev[i], par[i], f"relabelled {name} run_host_many #{i}")
+    level, parent, sigma = abfs.run_counts(G, s)
+    _check(g, s, level, parent, f"relabelled {name} counts")
+    assert np.array_equal(sigma.cpu().numpy().view(np.uint64), oracle.path_counts(g, s))
+    level, parent, tr = abfs.run_trace(G, s)
+    _check(g, s, level, parent, f"relabelled {name} trace")
+    best, _ = abfs.tune(G, _sources(g)[:2])
+    level, parent = abfs.run(G, s)
+    _check(g, s, level, parent, f"relabelled {name} tuned")
+    G.destroy()
+
+
 def test_run_host_many_matches(small):
     """Many searches into host memory: two device buffers alternate and each
     search's outputs are copied out while the next one runs, so the third and
@@ -480,6 +518,22 @@ def test_rmat22_16_sources(rmat22):
             level, parent, st = abfs.run(G, int(s), params=p, stats=True)
             assert st["status"] == 0
             _check(g, int(s), level, parent, f"rmat22 {kw} src{s}")
+
+
+def test_rmat22_relabelled(rmat22):
+    """The same graph relabelled by descending column length: the levels and the
+    least-index parents, in the input's labels, are the oracle's."""
+    g, _ = rmat22
+    G = abfs.graph_create(g.colptr, g.rowidx, directed=False)
+    abfs.graph_relabel(G)
+    srcs = synth.sources_with_degree(g, 16, seed=1)
+    for kw in (dict(mode=SUB), dict(mode=SUB, shrink_theta=0.6, shrink_max=1),
+               dict(mode=SUB, cluster_ctas=16), dict(mode=PLAIN)):
+        for s in srcs[:3]:
+            level, parent, st = abfs.run(G, int(s), params=_params(**kw), stats=True)
+            assert st["status"] == 0
+            _check(g, int(s), level, parent, f"rmat22 relabelled {kw} src{s}")
+    G.destroy()
 
 
 def test_rmat22_batch_64_sources(rmat22):
