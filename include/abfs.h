@@ -187,12 +187,13 @@ int abfs_graph_info(abfs_graph_t g, uint32_t* n, uint64_t* nnz, int* directed);
  * the empty ones last; input order inside each class.  On graphs with a
  * skewed degree distribution the mask tests and claims of the high-degree
  * rows then fall on few cache lines.  Graphs whose input order carries
- * locality (grids, geometric graphs) gain nothing from it.  Single searches in submatrix mode
- * without path counts (abfs_run, abfs_run_host, abfs_run_host_many,
- * abfs_run_trace, and the autotuner's trials) run on the copy; a last pass
- * writes level[] and parent[] in the input's labels, with the same least-index
- * parents (Theorem 1).  Path counts, the hybrid's bottom-up levels, the
- * comparator, batches, serving and abfs_run_static keep the input numbering.
+ * locality (grids, geometric graphs) gain nothing from it.  Single searches
+ * in submatrix mode without path counts (abfs_run, abfs_run_host,
+ * abfs_run_host_many, abfs_run_trace, and the autotuner's trials) run on the
+ * copy; a last pass writes level[] and parent[] in the input's labels, with
+ * the same least-index parents (Theorem 1).  Path counts, the hybrid (when
+ * the graph allows its bottom-up levels: undirected, ascending columns), the
+ * comparator, batches and serving keep the input numbering.
  * Costs a second copy of colptr/rowidx plus 8n bytes of label maps, and 8n
  * bytes more per workspace.  Builds on the host (the CSC is copied out and
  * back); synchronises; calling it again does nothing.  Returns ABFS_ERR_OOM or

@@ -498,8 +498,11 @@ int enqueue_single(abfs_graph_s* g, uint32_t source, int32_t* level, int32_t* pa
     if (rc) return rc;
     Workspace& w = g->ws;
     if (g->used) CK(cudaStreamWaitEvent(s, g->last_use, 0));
-    // submatrix searches without path counts run on the relabelled copy
-    const bool rel = w.relabel && p.mode == ABFS_MODE_SUBMATRIX && !sigma;
+    // submatrix searches without path counts run on the relabelled copy, except
+    // those that may take bottom-up levels: their scans need each column in
+    // ascending input-label order, which only the input numbering has
+    const bool bu_wanted = p.bottom_up_alpha && !g->directed && g->sorted;
+    const bool rel = w.relabel && p.mode == ABFS_MODE_SUBMATRIX && !sigma && !bu_wanted;
     const uint32_t bu_ok = (!rel && !g->directed && g->sorted && !sigma) ? 1u : 0u;
     EngineArgs a;
     a.insts = rel ? w.d_inst_r : w.d_inst;

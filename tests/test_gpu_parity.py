@@ -224,10 +224,10 @@ RELABEL = ["rmat_14", "er_2000", "grid_100x37", "rgg_2_15", "star", "path_3000",
 
 @pytest.mark.parametrize("name", RELABEL)
 def test_relabelled_graph_all_modes(small, name):
-    """A graph relabelled by descending column length (abfs_graph_relabel): every
+    """A graph relabelled by column-length class (abfs_graph_relabel): every
     mode equals the oracle in the input's labels -- the submatrix searches run
     on the copy (wide, reduction, resident, cluster and shrink paths), the
-    comparator, the hybrid and path counts keep the input numbering."""
+    comparator, the hybrid, path counts and batches keep the input numbering."""
     gs, _ = small
     g = gs[name]
     G = abfs.graph_create(g.colptr, g.rowidx, directed=g.directed)
@@ -254,6 +254,12 @@ def test_relabelled_graph_all_modes(small, name):
     best, _ = abfs.tune(G, _sources(g)[:2])
     level, parent = abfs.run(G, s)
     _check(g, s, level, parent, f"relabelled {name} tuned")
+    srcs = _sources(g)
+    levels, parents, st = abfs.run_batch([G] * len(srcs), srcs)
+    torch.cuda.synchronize()
+    assert all(x == 0 for x in st), st
+    for i, s in enumerate(srcs):
+        _check(g, s, levels[i], parents[i], f"relabelled {name} batch #{i}")
     G.destroy()
 
 
@@ -421,6 +427,12 @@ def test_hybrid_runs_bottom_up_only_where_allowed():
     level, parent, sigma = abfs.run_counts(G, s, params=p)
     _check(g, s, level, parent, "hybrid with counts")
     assert np.array_equal(sigma.cpu().numpy().view(np.uint64), oracle.path_counts(g, s))
+    # relabelled, the graph still offers the hybrid its bottom-up levels: such
+    # searches keep the input numbering, whose columns ascend
+    abfs.graph_relabel(G)
+    level, parent, trace = abfs.run_trace(G, s, params=p)
+    assert "bottom_up" in _kinds(trace)
+    _check(g, s, level, parent, "relabelled hybrid")
     G.destroy()
     # the same graph with each column's rows in a seeded random order
     rng = np.random.default_rng(7)
@@ -521,7 +533,7 @@ def test_rmat22_16_sources(rmat22):
 
 
 def test_rmat22_relabelled(rmat22):
-    """The same graph relabelled by descending column length: the levels and the
+    """The same graph relabelled by column-length class: the levels and the
     least-index parents, in the input's labels, are the oracle's."""
     g, _ = rmat22
     G = abfs.graph_create(g.colptr, g.rowidx, directed=False)
