@@ -201,6 +201,21 @@ int abfs_graph_info(abfs_graph_t g, uint32_t* n, uint64_t* nnz, int* directed);
  */
 int abfs_graph_relabel(abfs_graph_t g);
 
+/*
+ * The numbering abfs_graph_relabel uses, computed on the host from a CSC
+ * column pointer array alone (no GPU, no allocation visible to the caller):
+ * lab[i] = the input label of internal vertex i, pos[v] = the internal label
+ * of input vertex v (inverse permutations), both caller-owned host arrays of
+ * n entries.  Classes in internal order: (0) the longest columns, whole groups
+ * of equal length taken from the longest down while they hold at most n/64
+ * vertices in all; (1) further whole groups while classes 0-1 hold at most
+ * n/8; (2) the other non-empty columns; (3) the empty columns.  Input order
+ * inside each class.  colptr: host, n + 1 non-decreasing entries.  Returns
+ * ABFS_ERR_INVALID_ARG for a NULL pointer (n > 0) or a decreasing colptr;
+ * n = 0 does nothing.
+ */
+int abfs_relabel_order(const uint32_t* colptr, uint32_t n, uint32_t* lab, uint32_t* pos);
+
 /* Device bytes one search on this graph needs beyond the graph itself
  * (bitmaps, frontier queues, control), for the given parameters
  * (NULL = defaults).  Serving admission uses this figure. */

@@ -28,6 +28,7 @@ from .binding import (  # noqa: F401
     run_host,
     run_host_many,
     graph_relabel,
+    relabel_order,
     run_trace,
     strerror,
     tune,

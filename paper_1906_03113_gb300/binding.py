@@ -158,6 +158,7 @@ def load():
         "abfs_calibrate": ([u32, P(Calibration), vp], c_int),
         "abfs_run_host": ([vp, u32, vp, vp, vp, P(Params), P(Stats)], c_int),
         "abfs_graph_relabel": ([vp], c_int),
+        "abfs_relabel_order": ([vp, u32, vp, vp], c_int),
         "abfs_run_host_many": ([vp, P(u32), u32, vp, vp, vp, P(Params), P(i32)], c_int),
         "abfs_run_trace": ([vp, u32, vp, vp, vp, P(Params), vp, u32, P(u32)], c_int),
         "abfs_run_batch": ([P(vp), P(u32), u32, P(vp), P(vp), vp, P(Params), P(i32)], c_int),
@@ -396,6 +397,19 @@ def graph_relabel(g: Graph) -> None:
     """abfs_graph_relabel: single searches on g run on a copy numbered by
     column-length class; outputs stay in g's labels."""
     _check(load().abfs_graph_relabel(g.handle), "abfs_graph_relabel")
+
+
+def relabel_order(colptr):
+    """abfs_relabel_order (host only): (lab, pos) of the numbering
+    abfs_graph_relabel uses -- lab[i] is the input label of internal vertex i,
+    pos its inverse."""
+    cp = np.ascontiguousarray(colptr, dtype=np.uint32)
+    n = cp.size - 1
+    lab = np.empty(max(n, 0), dtype=np.uint32)
+    pos = np.empty(max(n, 0), dtype=np.uint32)
+    _check(load().abfs_relabel_order(cp.ctypes.data, max(n, 0), lab.ctypes.data, pos.ctypes.data),
+           "abfs_relabel_order")
+    return lab, pos
 
 
 def run_host_many(g: Graph, sources, level_host=None, parent_host=None, stream=None,

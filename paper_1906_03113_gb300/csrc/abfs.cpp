@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
+#include <functional>
 #include <mutex>
 #include <sstream>
 #include <string>
@@ -661,6 +662,55 @@ extern "C" int abfs_graph_destroy(abfs_graph_t g) {
     return ABFS_OK;
 }
 
+extern "C" int abfs_relabel_order(const uint32_t* colptr, uint32_t n, uint32_t* lab, uint32_t* pos) {
+    if (n == 0) return ABFS_OK;
+    if (!colptr || !lab || !pos) return ABFS_ERR_INVALID_ARG;
+    const uint32_t* cp = colptr;
+    for (uint32_t v = 0; v < n; ++v)
+        if (cp[v + 1] < cp[v]) return ABFS_ERR_INVALID_ARG;
+    // internal label of each vertex: by class, and in input order inside a
+    // class -- (0) the longest columns, whole length groups of at most n/64
+    // vertices in all; (1) the next longest, up to n/8 with class 0; (2) the
+    // other non-empty columns; (3) the empty ones.  The hubs the first levels
+    // reach share cache lines of every per-vertex array; the input order
+    // inside a class keeps whatever locality the input numbering had.
+    std::vector<uint32_t> len(n);
+    for (uint32_t v = 0; v < n; ++v) len[v] = cp[v + 1] - cp[v];
+    const uint64_t cap[2] = {(uint64_t)n / 64, (uint64_t)n / 8};
+    // the k = n/8 + 1 longest lengths, descending, place both thresholds: a
+    // length group that reaches index k - 1 holds more than n/8 vertices
+    const size_t k = (size_t)std::min<uint64_t>(n, cap[1] + 1);
+    std::vector<uint32_t> top(len);
+    std::nth_element(top.begin(), top.begin() + (k - 1), top.end(), std::greater<uint32_t>());
+    std::sort(top.begin(), top.begin() + k, std::greater<uint32_t>());
+    // thr[c]: the shortest length in classes 0..c (no class: above every length)
+    uint64_t thr[2];
+    size_t i = 0;  // vertices in the classes so far
+    for (int c = 0; c < 2; ++c) {
+        while (i < k && top[i] > 0) {
+            size_t j = i;
+            while (j < k && top[j] == top[i]) ++j;
+            if ((j == k && k < n) || j > cap[c]) break;  // the group does not fit
+            i = j;
+        }
+        thr[c] = i > 0 ? top[i - 1] : (uint64_t)UINT32_MAX + 1;
+    }
+    std::vector<uint8_t> cls(n);
+    uint64_t start[5] = {0, 0, 0, 0, 0};
+    for (uint32_t v = 0; v < n; ++v) {
+        const uint32_t d = len[v];
+        cls[v] = d >= thr[0] ? 0 : (d >= thr[1] ? 1 : (d > 0 ? 2 : 3));
+        ++start[cls[v] + 1];
+    }
+    for (int c = 1; c < 5; ++c) start[c] += start[c - 1];
+    for (uint32_t v = 0; v < n; ++v) {
+        const uint32_t i = (uint32_t)start[cls[v]]++;
+        lab[i] = v;
+        pos[v] = i;
+    }
+    return ABFS_OK;
+}
+
 extern "C" int abfs_graph_relabel(abfs_graph_t g) {
     if (!g) return ABFS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g->mu);
@@ -671,40 +721,10 @@ extern "C" int abfs_graph_relabel(abfs_graph_t g) {
     std::vector<uint32_t> cp((size_t)n + 1), rows(std::max<uint64_t>(nnz, 1));
     CK(cudaMemcpy(cp.data(), g->d_colptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost));
     if (nnz) CK(cudaMemcpy(rows.data(), g->d_rowidx, nnz * 4, cudaMemcpyDeviceToHost));
-    // internal label of each vertex: by class, and in input order inside a
-    // class -- (0) the longest columns, whole length groups of at most n/64
-    // vertices in all; (1) the next longest, up to n/8 with class 0; (2) the
-    // other non-empty columns; (3) the empty ones.  The hubs the first levels
-    // reach share cache lines of every per-vertex array; the input order
-    // inside a class keeps whatever locality the input numbering had.
-    uint32_t maxdeg = 0;
-    for (uint32_t v = 0; v < n; ++v) maxdeg = std::max(maxdeg, cp[v + 1] - cp[v]);
-    std::vector<uint64_t> hist((size_t)maxdeg + 1, 0);
-    for (uint32_t v = 0; v < n; ++v) ++hist[cp[v + 1] - cp[v]];
-    // thr[c]: the shortest length in classes 0..c (length groups kept whole)
-    uint32_t thr[2];
-    {
-        const uint64_t cap[2] = {(uint64_t)n / 64, (uint64_t)n / 8};
-        uint64_t acc = 0;
-        uint32_t t = maxdeg + 1;
-        for (int c = 0; c < 2; ++c) {
-            while (t > 1 && acc + hist[t - 1] <= cap[c]) acc += hist[--t];
-            thr[c] = t;
-        }
-    }
-    std::vector<uint8_t> cls(n);
-    uint64_t start[5] = {0, 0, 0, 0, 0};
-    for (uint32_t v = 0; v < n; ++v) {
-        const uint32_t d = cp[v + 1] - cp[v];
-        cls[v] = d >= thr[0] ? 0 : (d >= thr[1] ? 1 : (d > 0 ? 2 : 3));
-        ++start[cls[v] + 1];
-    }
-    for (int c = 1; c < 5; ++c) start[c] += start[c - 1];
     std::vector<uint32_t> lab(n), pos(n);
-    for (uint32_t v = 0; v < n; ++v) {
-        const uint32_t i = (uint32_t)start[cls[v]]++;
-        lab[i] = v;
-        pos[v] = i;
+    {
+        const int rc0 = abfs_relabel_order(cp.data(), n, lab.data(), pos.data());
+        if (rc0) return rc0;
     }
     // the relabelled CSC: column i is column lab[i], its rows renamed
     std::vector<uint32_t> rcp((size_t)n + 1), rrows(std::max<uint64_t>(nnz, 1));
