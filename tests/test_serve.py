@@ -101,6 +101,22 @@ def test_serve_mix_equals_alone(graphs):
 
 
 @pytest.mark.gpu
+def test_serve_on_relabelled_graphs(graphs):
+    """Served queries on graphs that carry a relabelled copy run on the input
+    numbering; abfs_run of the same query runs on the copy; both equal the
+    oracle."""
+    gs, _ = graphs
+    sub = [gs[1], gs[3], gs[4]]
+    dev = [abfs.graph_create(g.colptr, g.rowidx, directed=g.directed) for g in sub]
+    for G in dev:
+        abfs.graph_relabel(G)
+    cfg = abfs.serve_default_cfg(max_slots=16, memory_budget=2 << 30, idle_exit_ms=20)
+    _serve_and_check(sub, dev, _queries(sub, 60, 5), cfg, bursts=3)
+    for G in dev:
+        G.destroy()
+
+
+@pytest.mark.gpu
 def test_serve_memory_gated_admission(graphs):
     gs, dev = graphs
     # a budget that holds only one or two queries of the largest graph at a time
