@@ -17,6 +17,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/abfs.h"
@@ -726,13 +727,34 @@ extern "C" int abfs_graph_relabel(abfs_graph_t g) {
         const int rc0 = abfs_relabel_order(cp.data(), n, lab.data(), pos.data());
         if (rc0) return rc0;
     }
-    // the relabelled CSC: column i is column lab[i], its rows renamed
+    // the relabelled CSC: column i is column lab[i], its rows renamed (in the
+    // input's order; no search on the copy depends on the row order).
+    // Columns are filled by several host threads.
     std::vector<uint32_t> rcp((size_t)n + 1), rrows(std::max<uint64_t>(nnz, 1));
     rcp[0] = 0;
-    for (uint32_t i = 0; i < n; ++i) {
-        const uint32_t v = lab[i], b = cp[v], len = cp[v + 1] - b;
-        for (uint32_t x = 0; x < len; ++x) rrows[(size_t)rcp[i] + x] = pos[rows[(size_t)b + x]];
-        rcp[i + 1] = rcp[i] + len;
+    for (uint32_t i = 0; i < n; ++i) rcp[i + 1] = rcp[i] + (cp[lab[i] + 1] - cp[lab[i]]);
+    {
+        auto fill = [&](uint32_t i0, uint32_t i1) {
+            for (uint32_t i = i0; i < i1; ++i) {
+                const uint32_t b = cp[lab[i]];
+                uint32_t* out = rrows.data() + rcp[i];
+                const uint32_t len = rcp[i + 1] - rcp[i];
+                for (uint32_t x = 0; x < len; ++x) out[x] = pos[rows[(size_t)b + x]];
+            }
+        };
+        const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        // column ranges of about nnz / nt entries each
+        uint32_t i0 = 0;
+        for (unsigned t = 1; t <= nt && i0 < n; ++t) {
+            const uint64_t goal = nnz * t / nt;
+            uint32_t i1 = (uint32_t)(std::upper_bound(rcp.begin() + i0, rcp.end(), (uint32_t)goal) -
+                                     rcp.begin());
+            i1 = t == nt ? n : std::min(std::max(i1, i0 + 1), n);
+            th.emplace_back(fill, i0, i1);
+            i0 = i1;
+        }
+        for (auto& x : th) x.join();
     }
     const uint32_t nwords = (n + 31) / 32;
     int rc = dev_alloc((void**)&g->r_colptr, ((size_t)n + 1) * 4);
